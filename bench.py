@@ -1,0 +1,387 @@
+"""Benchmark: propagation of a batch of search-tree nodes to their fixed points.
+
+Workload (the propagation-batch configuration): one seeded 30-task, 4-resource
+scheduling model (931 variables, ~1,060 propagator rows) and 10,000 search
+nodes, each the root store narrowed by 0-15 random branching decisions.  One
+step propagates all 10,000 stores through the C ABI (pccp_propagate), in
+place, from pristine copies restored before every step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank propagates its own
+10,000-node batch (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synthetic import config_instance, draw_partial_assignments  # noqa: E402
+
+N_NODES = 10_000
+NODE_SEED = 1
+FAMILY, INSTANCE = "j30", 0
+METRIC = "search nodes/s"
+UNIT = "nodes/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_config(n_vars, rows, extra=None):
+    cfg = {"workload": f"propagation batch: {N_NODES} search nodes (0-15 decisions each) of a "
+                       f"seeded 30-task 4-resource scheduling model ({n_vars} vars, {rows} rows)",
+           "model": f"{FAMILY}/{INSTANCE}", "nodes_per_step": N_NODES, "node_seed": NODE_SEED,
+           "l2": "flushed between steps (256 MB write); stores restored from pristine copies"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def build_inputs():
+    inst = config_instance(FAMILY, INSTANCE)
+    nodes = draw_partial_assignments(inst.n, inst.horizon, N_NODES, seed=NODE_SEED)
+    return inst, nodes
+
+
+# ------------------------------------------------------------ CPU oracle leg
+
+def oracle_rate(inst, nodes, n_sample, threads):
+    """Time the CPU oracle (as it stands) on the first n_sample nodes, split
+    over `threads` Python threads (the C oracle releases the GIL)."""
+    import oracle
+    from oracle.rcpsp import rcpsp_model, node_store
+    from concurrent.futures import ThreadPoolExecutor
+    om = rcpsp_model(inst)
+    sample = nodes[:n_sample]
+    lb = np.array([node_store(om, d)[0] for d in sample])
+    ub = np.array([node_store(om, d)[1] for d in sample])
+    chunks = np.array_split(np.arange(len(sample)), threads)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda ix: oracle.propagate_batch(om, lb[ix], ub[ix]), chunks))
+    dt = time.perf_counter() - t0
+    return len(sample) / dt, dt
+
+
+def cpu_baseline(inst, nodes, target_s=12.0):
+    """The oracle on the host cores: a 1-thread rate on 1,500 nodes, then the
+    whole 10,000-node batch repeated until about target_s of wall time over
+    all cores."""
+    cores = os.cpu_count() or 1
+    r1, t1 = oracle_rate(inst, nodes, 1500, 1)
+    passes = max(1, int(round(target_s * r1 * cores / N_NODES)))
+    rN, tN = oracle_rate(inst, nodes * passes, N_NODES * passes, cores)
+    return {"value": rN, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the {N_NODES}-node batch x {passes} over {cores} threads ({tN:.1f} s); "
+                      f"1 thread: {r1:.1f} nodes/s on the first 1500 nodes ({t1:.1f} s)",
+            "value_1core": r1}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step propagates a bounded
+    sample of the same workload on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inst, nodes = build_inputs()
+    import oracle
+    from oracle.rcpsp import rcpsp_model, node_store
+    from concurrent.futures import ThreadPoolExecutor
+    om = rcpsp_model(inst)
+    cores = os.cpu_count() or 1
+    per_step = 64 * cores
+    lb = np.array([node_store(om, d)[0] for d in nodes[:per_step]])
+    ub = np.array([node_store(om, d)[1] for d in nodes[:per_step]])
+    chunks = np.array_split(np.arange(per_step), cores)
+
+    def step():
+        with ThreadPoolExecutor(cores) as ex:
+            list(ex.map(lambda ix: oracle.propagate_batch(om, lb[ix], ub[ix]), chunks))
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * statistics.mean(times)
+    value = per_step / (ms / 1000)
+    rows = om.temporal and (len(om.temporal) + len(om.reified) + len(om.linear))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": workload_config(om.n_vars, rows, {"sample_nodes_per_step": per_step}),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                             "sample": f"first {per_step} of the {N_NODES} nodes per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU leg
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def snapshot(self):
+        """One query, for a timed region shorter than the sampling period."""
+        try:
+            out = subprocess.run(["nvidia-smi", f"--id={self.device_index}",
+                                  f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                                 capture_output=True, text=True, timeout=20).stdout
+            self.lines += [ln.strip() for ln in out.splitlines() if ln.strip()]
+            self.note = "one query at the end of a timed region shorter than the 100 ms period"
+        except (OSError, subprocess.TimeoutExpired):
+            pass
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        if not self.lines:
+            self.snapshot()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        out = {"sm_mhz": statistics.median(sm) if sm else None,
+               "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+               "samples": len(sm)}
+        if getattr(self, "note", None):
+            out["note"] = self.note
+        return out
+
+
+def launch_desc(args):
+    if not (args.team or args.teams or args.ctas_per_sm or args.linear_mode):
+        return "library default"
+    return {"team_threads": args.team, "teams_per_cta": args.teams,
+            "ctas_per_sm": args.ctas_per_sm, "linear_mode": args.linear_mode}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2207_12116_gb300 as pccp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    inst, nodes = build_inputs()
+    rows = pccp.rcpsp.build_rows(inst)
+    model = pccp.Model.from_rows(rows)
+    lb_h, ub_h = pccp.rcpsp.node_stores(rows, nodes)
+    nv = model.n_vars
+    pristine_lb = torch.from_numpy(lb_h).to(dev)
+    pristine_ub = torch.from_numpy(ub_h).to(dev)
+    lb = pristine_lb.clone()
+    ub = pristine_ub.clone()
+    status = torch.empty(N_NODES, dtype=torch.int32, device=dev)
+    iters = torch.empty(N_NODES, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    cfg = None
+    if args.team or args.teams or args.ctas_per_sm or args.linear_mode:
+        cfg = pccp.launch_config(args.team, args.teams, args.ctas_per_sm, 0, args.linear_mode)
+
+    def prepare():
+        lb.copy_(pristine_lb)
+        ub.copy_(pristine_ub)
+        flush.fill_(1)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 0)):
+        prepare()
+        pccp.propagate(model, lb, ub, status, iters, config=cfg)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        prepare()
+        ev[k][0].record(stream)
+        pccp.propagate(model, lb, ub, status, iters, config=cfg)
+        ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    kernel_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(kernel_ms)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+
+    st = status.cpu().numpy()
+    it = iters.cpu().numpy().astype(np.int64)
+    rows_per_sweep = model.rows
+    evals = int(it.sum()) * rows_per_sweep
+    bytes_smem = int(it.sum()) * int(model.info.bytes_per_sweep)
+    io_bytes = 4 * nv * N_NODES * 4 + 8 * N_NODES  # read+write lb, ub; status, iterations
+
+    e2e = None
+    if not args.no_e2e:
+        if cfg is not None:
+            raise SystemExit("--no-e2e is required with an explicit launch shape")
+        # end to end through the public API: pinned host stores in, results out
+        lb_pin = torch.from_numpy(lb_h).pin_memory()
+        ub_pin = torch.from_numpy(ub_h).pin_memory()
+        out_lb = torch.empty_like(lb_pin).pin_memory()
+        out_ub = torch.empty_like(ub_pin).pin_memory()
+        out_st = torch.empty(N_NODES, dtype=torch.int32).pin_memory()
+        e2e_ms = []
+        n_e2e = min(args.steps, 100)
+        for k in range(max(args.warmup, 0) + n_e2e):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lb.copy_(lb_pin, non_blocking=True)
+            ub.copy_(ub_pin, non_blocking=True)
+            pccp.propagate(model, lb, ub, status, iters, config=cfg)
+            out_lb.copy_(lb, non_blocking=True)
+            out_ub.copy_(ub, non_blocking=True)
+            out_st.copy_(status, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            if k >= args.warmup:
+                e2e_ms.append(a.elapsed_time(b))
+        e2e_t = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        e2e_v = world * N_NODES / (float(e2e_t.item()) / 1000)
+        assert np.array_equal(out_st.numpy(), st), "end-to-end results differ from device-timed run"
+        e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * nv * N_NODES,
+               "d2h_bytes_per_step": 2 * 4 * nv * N_NODES + 4 * N_NODES}
+
+    if rank == 0:
+        peaks = load_peaks()
+        props = torch.cuda.get_device_properties(dev)
+        sms = props.multi_processor_count
+        sm_mhz = clk.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median")
+        smem_peak = sms * 128 * (sm_mhz or 0) * 1e6 / 1e9  # GB/s: 128 B/clk/SM
+        achieved = bytes_smem / (ms / 1000) / 1e9
+        hbm_peak = peaks.get("hbm_gbs")
+        line = {
+            "metric": METRIC, "value": world * N_NODES / (ms_max / 1000), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": workload_config(nv, rows_per_sweep, {"parallelism": f"replicas{world}",
+                                                           "launch": launch_desc(args)}),
+            "propagator_evals_per_s": world * evals / (ms_max / 1000),
+            "fixpoint_iterations_per_node": float(it.mean()),
+            "failed_nodes": int((st == 1).sum()),
+            "roofline": {"bound": "smem", "achieved": achieved, "peak": smem_peak,
+                         "unit": "GB/s", "frac": achieved / smem_peak if smem_peak else None,
+                         "traffic": None,
+                         "peak_source": f"derived: {sms} SMs x 128 B/clk x {sm_mhz} MHz "
+                                        f"(median SM clock sampled during the run)",
+                         "algorithmic_bytes_per_launch": bytes_smem,
+                         "hbm": {"io_bytes_per_launch": io_bytes,
+                                 "achieved": io_bytes / (ms / 1000) / 1e9,
+                                 "peak": hbm_peak, "peak_source": "of measured (MEASURED_PEAKS.json)"}},
+            "cpu_baseline": None,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "wall_s_timed_loop": wall,
+            "kernel_ms_min": min(kernel_ms), "kernel_ms_max": max(kernel_ms),
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(inst, nodes)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--team", type=int, default=0, help="threads per team (0: library default)")
+    ap.add_argument("--teams", type=int, default=0, help="teams per CTA (0: library default)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--linear-mode", type=int, default=0, help="1 warp/row, 2 thread/row")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

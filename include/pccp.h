@@ -1,0 +1,223 @@
+/*
+ * pccp.h -- C ABI of the GB300 (sm_103a) PCCP propagate-and-search library.
+ *
+ * The method: a constraint model is compiled to guarded commands over a store
+ * of integer intervals (the lattice IZ = ZInc x ZDec, paper Sec. 2; the
+ * guarded normal form of Sec. 3, Prop. 3).  Propagation joins every command's
+ * tell into the store until nothing changes (the least fixed point of
+ * Theorem 1, reached by any fair order: Def. 4 and the fix D = fix O
+ * theorem).  On the GPU the commands of one store run concurrently with no
+ * locks; every tell is an atomic max on a lower bound or an atomic min on an
+ * upper bound in shared memory (the load/store semantics of Sec. 4, whose
+ * soundness and completeness theorems make the result independent of the
+ * interleaving).  Search is propagate-and-branch with full recomputation from
+ * a root store (Sec. 5, "Turbo").
+ *
+ * Conventions for every call:
+ *  - Return 0 (PCCP_OK) on success and a negative PCCP_ERR_* code otherwise;
+ *    pccp_error_string() names the code.  No call aborts the process.
+ *  - Host pointers are read during the call only; the caller keeps ownership.
+ *    Device pointers stay owned by the caller and must stay valid until the
+ *    work queued on the stream has finished.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  The work runs on the device that is current at the call, which
+ *    must be the device the model was created on.
+ *  - All values are int32.  Variable indices are 0-based.
+ */
+#ifndef PCCP_H
+#define PCCP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define PCCP_OK 0
+#define PCCP_ERR_INVALID (-1)  /* bad argument: index out of range, lb0 > ub0, empty
+                                  linear row, reified b not Boolean, NULL pointer ... */
+#define PCCP_ERR_OVERFLOW (-2) /* some intermediate of a propagator could leave int32 */
+#define PCCP_ERR_SMEM (-3)     /* model (table + stores) does not fit shared memory */
+#define PCCP_ERR_TIMEOUT (-4)  /* a device-side wait or iteration budget ran out */
+#define PCCP_ERR_CUDA (-5)     /* a CUDA runtime call failed */
+#define PCCP_ERR_UNSUPPORTED (-6) /* valid model outside this build's packed limits
+                                     (> 65535 variables, |coef| > 32767, ...) */
+
+/* ---- per-store status written by pccp_propagate ------------------------ */
+#define PCCP_FIXPOINT 0 /* lb/ub hold the least fixed point */
+#define PCCP_FAILED 1   /* some interval became empty; lb/ub contents unspecified */
+#define PCCP_ERROR 2    /* iteration budget exhausted; lb/ub contents unspecified */
+
+/* ---- model ------------------------------------------------------------- */
+
+/* A constraint model: the PCCP program of one problem instance (Sec. 2).
+ *
+ * Variables 0..n_vars-1 have root domains [lb0[v], ub0[v]] (lb0 <= ub0).
+ * Three row kinds, each compiled to guarded commands:
+ *   temporal  {x, y, d}      : x + d <= y.  The compilation [[x + y <= c]] of
+ *                              Sec. 2 with y negated: ub(x) <= ub(y) - d and
+ *                              lb(y) >= lb(x) + d.
+ *   linear    c, terms       : sum_k coef_k * var_k <= c.  The resource-sum
+ *                              compilation of Sec. 2, generalised to any
+ *                              coefficient sign: each term is bounded by c
+ *                              minus the minimum of the other terms
+ *                              (the term itself is excluded from that sum).
+ *                              Rows are CSR: terms linear_off[i] ..
+ *                              linear_off[i+1]-1; zero coefficients are dropped;
+ *                              a row must keep at least one term.
+ *   reified   {b, x, y, d}   : b <=> (x <= y and y < x + d), the overlap Booleans
+ *                              of the scheduling model (Sec. 2), compiled as the
+ *                              four asks of [[phi <=> psi]]; b's root domain must
+ *                              lie within [0, 1].
+ * objective: variable minimised by pccp_solve (-1: stop at the first solution).
+ * branch_vars: variables search branches on, in input order.
+ * All arrays are host memory, copied by pccp_model_create.                 */
+typedef struct {
+  int32_t n_vars;
+  const int32_t* lb0;        /* [n_vars] */
+  const int32_t* ub0;        /* [n_vars] */
+  int32_t n_temporal;
+  const int32_t* temporal;   /* [n_temporal][3] = {x, y, d} */
+  int32_t n_linear;
+  const int32_t* linear_c;   /* [n_linear] */
+  const int32_t* linear_off; /* [n_linear + 1], linear_off[0] = 0 */
+  const int32_t* term_coef;  /* [linear_off[n_linear]] */
+  const int32_t* term_var;   /* [linear_off[n_linear]] */
+  int32_t n_reified;
+  const int32_t* reified;    /* [n_reified][4] = {b, x, y, d} */
+  int32_t objective;
+  int32_t n_branch;
+  const int32_t* branch_vars; /* [n_branch] */
+} pccp_model_desc;
+
+typedef struct pccp_model pccp_model; /* opaque; owns a device copy of the table */
+
+/* Validates `desc`, packs its rows into the structure-of-arrays propagator
+ * table (the guarded normal form of Sec. 3) and copies it to the current
+ * device (synchronously).  On success *out receives a model that must be
+ * released with pccp_model_destroy.  Errors: INVALID, OVERFLOW, UNSUPPORTED,
+ * CUDA (then *out is NULL). */
+int pccp_model_create(const pccp_model_desc* desc, pccp_model** out);
+
+/* Frees the model and its device table (synchronises the device first).
+ * NULL is accepted. */
+void pccp_model_destroy(pccp_model* model);
+
+/* Sizes of a created model, for planning buffers and roofline accounting. */
+typedef struct {
+  int32_t n_vars;
+  int32_t n_temporal, n_linear, n_terms, n_reified;
+  int32_t table_bytes;      /* packed table copied to shared memory per CTA */
+  int64_t bytes_per_sweep;  /* algorithmic bytes of one evaluation of every row:
+                               temporal 20, reified 40, linear 12 + 12 * len */
+  int32_t max_store_vars;   /* largest n_vars a single CTA can stage */
+} pccp_model_info;
+
+int pccp_model_get_info(const pccp_model* model, pccp_model_info* info);
+
+/* ---- propagation ------------------------------------------------------- */
+
+/* Propagates a batch of stores to their least fixed points, in place.
+ *   lb, ub     : DEVICE int32 arrays [n_stores][n_vars] (row-major).  Each
+ *                store is first joined with the model's root domains; the
+ *                result is the least fixed point above that (Theorem 1).
+ *   status     : DEVICE int32 [n_stores]: PCCP_FIXPOINT / PCCP_FAILED /
+ *                PCCP_ERROR.  lb/ub of a non-FIXPOINT store are unspecified.
+ *   iterations : DEVICE int32 [n_stores] or NULL: fixed-point iterations run
+ *                for each store (every row is evaluated once per iteration;
+ *                the loop is eventless, Sec. 5).
+ *   n_stores   : >= 0 (0 queues nothing).
+ * Asynchronous on `stream`.  Errors: INVALID, SMEM, CUDA.
+ * Calls on one model may run concurrently on different streams. */
+int pccp_propagate(const pccp_model* model, int32_t n_stores, int32_t* lb, int32_t* ub,
+                   int32_t* status, int32_t* iterations, void* stream);
+
+/* Launch shape of the propagation kernel.  A team (team_threads threads, whole
+ * warps) owns one store at a time; a CTA holds one copy of the propagator
+ * table in shared memory and teams_per_cta team stores.  Zero fields take the
+ * library's defaults.  The result does not depend on the shape (any fair
+ * interleaving reaches the same fixed point, Sec. 3). */
+typedef struct {
+  int32_t team_threads;   /* 32..1024, multiple of 32 */
+  int32_t teams_per_cta;  /* 1..15 (team_threads * teams_per_cta <= 1024) */
+  int32_t ctas_per_sm;    /* cap on resident CTAs per SM used for the grid */
+  int32_t max_iterations; /* per-store iteration budget (exceeded: PCCP_ERROR) */
+  int32_t linear_mode;    /* 0 default, 1 a warp per linear row, 2 a thread per row */
+} pccp_launch_config;
+
+/* pccp_propagate with an explicit launch shape (cfg may be NULL).  Returns
+ * PCCP_ERR_SMEM if the requested teams do not fit shared memory. */
+int pccp_propagate_ex(const pccp_model* model, int32_t n_stores, int32_t* lb, int32_t* ub,
+                      int32_t* status, int32_t* iterations, const pccp_launch_config* cfg,
+                      void* stream);
+
+/* ---- search ------------------------------------------------------------ */
+
+#define PCCP_INPUT_ORDER 0 /* lowest-index unfixed branch variable */
+#define PCCP_FIRST_FAIL 1  /* smallest ub - lb, ties to the lower index */
+
+#define PCCP_OPTIMISE 0  /* branch and bound on the objective */
+#define PCCP_COUNT_ALL 1 /* enumerate every solution (objective bounded by obj_ub) */
+
+/* Result status of a search. */
+#define PCCP_RES_OPTIMAL 0    /* tree exhausted, >= 1 solution (count-all: complete) */
+#define PCCP_RES_INFEASIBLE 1 /* tree exhausted, no solution */
+#define PCCP_RES_LIMIT 2      /* a node or time limit stopped the search */
+
+typedef struct {
+  int32_t strategy;      /* PCCP_INPUT_ORDER or PCCP_FIRST_FAIL */
+  int32_t mode;          /* PCCP_OPTIMISE or PCCP_COUNT_ALL */
+  int32_t deterministic; /* 1: one team walks the tree in the sequential DFS
+                            order, so node counts are reproducible; 0: many
+                            teams split the tree into subproblems and share
+                            the incumbent (node counts then vary) */
+  int32_t obj_ub;        /* inclusive upper bound told on the objective at every
+                            node; INT32_MAX for none */
+  int64_t node_limit;    /* stop after this many nodes (<= 0: none); per instance */
+  int64_t time_limit_ms; /* stop after this many ms of device time (<= 0: none) */
+  int32_t threads;       /* threads per team (multiple of 32, <= 1024; 0 = auto) */
+  int32_t blocks;        /* CTAs for the parallel search (0 = auto) */
+} pccp_solve_opts;
+
+/* Counters and outcome of one search.  A node is every store propagated,
+ * including the root and failed children.  Split rule: [l,u] at
+ * m = l + (u - l) / 2, left child ub <= m explored first, right lb >= m + 1;
+ * after a solution of objective z every later node is told ub(obj) <= z - 1. */
+typedef struct {
+  int32_t status;        /* PCCP_RES_* */
+  int32_t has_solution;
+  int32_t objective;     /* lb(objective) of the recorded solution */
+  int32_t* witness;      /* IN: HOST int32 [n_vars] buffer or NULL; OUT: lb of the
+                            recorded solution (optimise: the last improving
+                            one; count-all: the first found) */
+  int64_t nodes;
+  int64_t fails;
+  int64_t solutions;
+  int64_t iterations;    /* fixed-point iterations summed over nodes */
+  int64_t rows_evaluated;/* iterations x rows: propagator evaluations */
+  int32_t max_depth;
+  float elapsed_ms;      /* device time of the search kernel */
+} pccp_result;
+
+/* Solves one model.  Synchronous: returns after the result is filled.
+ * Errors: INVALID, SMEM, TIMEOUT (a device wait gave up), CUDA. */
+int pccp_solve(const pccp_model* model, const pccp_solve_opts* opts, pccp_result* result,
+               void* stream);
+
+/* Solves n_models models in one persistent launch; each model is searched by
+ * one team in the deterministic order (opts->deterministic is ignored and
+ * node_limit / time_limit_ms apply per model).  results[i] is filled for
+ * models[i] (its witness pointer is honoured).  Synchronous.
+ * Errors: INVALID, SMEM, TIMEOUT, CUDA. */
+int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
+                     const pccp_solve_opts* opts, pccp_result* results, void* stream);
+
+/* Human-readable name of a return code (static storage). */
+const char* pccp_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCCP_H */

@@ -1,0 +1,237 @@
+"""GB300 (sm_103a) PCCP propagate-and-search: Python binding of libpccp.so.
+
+The names mirror the C ABI of include/pccp.h.  This module only marshals
+arguments (numpy arrays for model rows, torch CUDA tensors for stores); every
+step of propagation and search runs in the CUDA library, and loading fails
+loudly when the library is missing.
+
+    m = Model.from_arrays(...) or Model.from_rcpsp(instance)
+    propagate(m, lb, ub)          # torch int32 CUDA tensors [n, n_vars], in place
+    solve(m) / solve_batch([m1, m2, ...])
+"""
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import (PCCP_OK, PCCP_ERR_INVALID, PCCP_ERR_OVERFLOW, PCCP_ERR_SMEM,  # noqa: F401
+                   PCCP_ERR_TIMEOUT, PCCP_ERR_CUDA, PCCP_ERR_UNSUPPORTED, PCCP_FIXPOINT,
+                   PCCP_FAILED, PCCP_ERROR, PCCP_INPUT_ORDER, PCCP_FIRST_FAIL, PCCP_OPTIMISE,
+                   PCCP_COUNT_ALL, PCCP_RES_OPTIMAL, PCCP_RES_INFEASIBLE, PCCP_RES_LIMIT,
+                   INT32_MAX, PccpError, check, load, library_path)
+from . import rcpsp  # noqa: F401
+
+__all__ = ["Model", "pccp_model_create", "pccp_model_destroy", "pccp_model_get_info",
+           "pccp_propagate", "pccp_propagate_ex", "pccp_solve", "pccp_solve_batch",
+           "pccp_error_string", "propagate", "propagate_host", "solve", "solve_batch",
+           "PccpError", "load", "library_path"]
+
+
+def _i32(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+    if a.size and (a.min() < -(1 << 31) or a.max() >= (1 << 31)):
+        raise PccpError(PCCP_ERR_OVERFLOW, "value outside int32")
+    a = a.astype(np.int32)
+    return a.reshape(shape) if shape is not None else a.reshape(-1)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else ctypes.c_void_p(0)
+
+
+# ------------------------------------------------------------- raw C names
+
+def pccp_model_create(desc):
+    h = ctypes.c_void_p()
+    rc = load().pccp_model_create(ctypes.byref(desc), ctypes.byref(h))
+    return rc, h
+
+
+def pccp_model_destroy(handle):
+    load().pccp_model_destroy(handle)
+
+
+def pccp_model_get_info(handle):
+    info = _abi.pccp_model_info()
+    rc = load().pccp_model_get_info(handle, ctypes.byref(info))
+    return rc, info
+
+
+def pccp_propagate(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr, stream):
+    return load().pccp_propagate(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr, stream)
+
+
+def pccp_propagate_ex(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr, cfg, stream):
+    return load().pccp_propagate_ex(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr,
+                                    ctypes.byref(cfg) if cfg is not None else None, stream)
+
+
+def pccp_solve(handle, opts, result, stream):
+    return load().pccp_solve(handle, ctypes.byref(opts), ctypes.byref(result), stream)
+
+
+def pccp_solve_batch(handles, opts, results, stream):
+    n = len(handles)
+    arr = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    return load().pccp_solve_batch(arr, n, ctypes.byref(opts), results, stream)
+
+
+def pccp_error_string(code):
+    return _abi.error_string(code)
+
+
+# ------------------------------------------------------------------- model
+
+class Model:
+    """A created pccp_model (device copy of the packed propagator table)."""
+
+    def __init__(self, lb0, ub0, temporal=None, linear_c=None, linear_off=None, term_coef=None,
+                 term_var=None, reified=None, objective=-1, branch=None):
+        self.lb0 = _i32(lb0)
+        self.ub0 = _i32(ub0)
+        self.n_vars = len(self.lb0)
+        self.temporal = _i32(temporal if temporal is not None else np.zeros((0, 3)), (-1, 3))
+        self.reified = _i32(reified if reified is not None else np.zeros((0, 4)), (-1, 4))
+        self.linear_c = _i32(linear_c if linear_c is not None else [])
+        self.linear_off = _i32(linear_off if linear_off is not None else [0])
+        self.term_coef = _i32(term_coef if term_coef is not None else [])
+        self.term_var = _i32(term_var if term_var is not None else [])
+        self.objective = int(objective)
+        self.branch = _i32(branch if branch is not None else [])
+        desc = _abi.pccp_model_desc(
+            self.n_vars, _ptr(self.lb0), _ptr(self.ub0),
+            len(self.temporal), _ptr(self.temporal),
+            len(self.linear_c), _ptr(self.linear_c), _ptr(self.linear_off),
+            _ptr(self.term_coef), _ptr(self.term_var),
+            len(self.reified), _ptr(self.reified),
+            self.objective, len(self.branch), _ptr(self.branch))
+        rc, h = pccp_model_create(desc)
+        check(rc, "pccp_model_create")
+        self.handle = h
+        rc, info = pccp_model_get_info(h)
+        check(rc, "pccp_model_get_info")
+        self.info = info
+
+    @classmethod
+    def from_rows(cls, rows):
+        return cls(rows["lb0"], rows["ub0"], rows["temporal"], rows["linear_c"],
+                   rows["linear_off"], rows["term_coef"], rows["term_var"], rows["reified"],
+                   rows["objective"], rows["branch"])
+
+    @classmethod
+    def from_rcpsp(cls, inst):
+        return cls.from_rows(rcpsp.build_rows(inst))
+
+    @classmethod
+    def from_lists(cls, lb0, ub0, temporal=(), linear=(), reified=(), objective=-1, branch=()):
+        """temporal [(x, y, d)], linear [(c, [(coef, var), ...])], reified [(b, x, y, d)]."""
+        off = [0]
+        coef, var = [], []
+        for _, terms in linear:
+            for a, v in terms:
+                coef.append(a)
+                var.append(v)
+            off.append(len(coef))
+        return cls(lb0, ub0, list(temporal) or np.zeros((0, 3)), [c for c, _ in linear], off,
+                   coef, var, list(reified) or np.zeros((0, 4)), objective, list(branch))
+
+    @property
+    def rows(self) -> int:
+        return int(self.info.n_temporal + self.info.n_reified + self.info.n_linear)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            pccp_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------- torch front end
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def launch_config(team_threads=0, teams_per_cta=0, ctas_per_sm=0, max_iterations=0,
+                  linear_mode=0):
+    return _abi.pccp_launch_config(team_threads, teams_per_cta, ctas_per_sm, max_iterations,
+                                   linear_mode)
+
+
+def propagate(model: Model, lb, ub, status=None, iterations=None, config=None, stream=None):
+    """Propagate the stores in place.  lb/ub: int32 CUDA tensors [n, n_vars]
+    (contiguous).  Returns (status, iterations) int32 CUDA tensors [n]."""
+    import torch
+    if lb.dtype != torch.int32 or ub.dtype != torch.int32 or not lb.is_cuda or not ub.is_cuda:
+        raise PccpError(PCCP_ERR_INVALID, "lb/ub must be int32 CUDA tensors")
+    if not lb.is_contiguous() or not ub.is_contiguous() or lb.shape != ub.shape:
+        raise PccpError(PCCP_ERR_INVALID, "lb/ub must be contiguous and of the same shape")
+    n = lb.shape[0] if lb.dim() == 2 else 1
+    if lb.numel() != n * model.n_vars:
+        raise PccpError(PCCP_ERR_INVALID, "store width differs from the model's variables")
+    if status is None:
+        status = torch.empty(n, dtype=torch.int32, device=lb.device)
+    if iterations is None:
+        iterations = torch.empty(n, dtype=torch.int32, device=lb.device)
+    sp = _stream_ptr(stream)
+    rc = pccp_propagate_ex(model.handle, n, ctypes.c_void_p(lb.data_ptr()),
+                           ctypes.c_void_p(ub.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                           ctypes.c_void_p(iterations.data_ptr()), config, sp)
+    check(rc, "pccp_propagate")
+    return status, iterations
+
+
+def propagate_host(model: Model, lb, ub, device="cuda", config=None, stream=None):
+    """End-to-end form: host (pinned) int32 tensors in, host tensors out.
+    Copies the stores to the device, propagates, copies the results back."""
+    import torch
+    dlb = lb.to(device, non_blocking=True)
+    dub = ub.to(device, non_blocking=True)
+    st, it = propagate(model, dlb, dub, config=config, stream=stream)
+    out = (dlb.to("cpu", non_blocking=False), dub.to("cpu"), st.to("cpu"), it.to("cpu"))
+    return out
+
+
+def _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks):
+    return _abi.pccp_solve_opts(strategy, mode, int(bool(deterministic)), obj_ub, node_limit,
+                                time_limit_ms, threads, blocks)
+
+
+def _result_dict(r, w):
+    return {"status": r.status, "has_solution": bool(r.has_solution),
+            "objective": int(r.objective) if r.has_solution else None,
+            "witness": w.copy() if r.has_solution else None,
+            "nodes": int(r.nodes), "fails": int(r.fails), "solutions": int(r.solutions),
+            "iterations": int(r.iterations), "rows_evaluated": int(r.rows_evaluated),
+            "max_depth": int(r.max_depth), "elapsed_ms": float(r.elapsed_ms)}
+
+
+def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, deterministic=True,
+          obj_ub=INT32_MAX, node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None):
+    o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks)
+    w = np.zeros(model.n_vars, dtype=np.int32)
+    r = _abi.pccp_result()
+    r.witness = w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    rc = pccp_solve(model.handle, o, r, _stream_ptr(stream))
+    check(rc, "pccp_solve")
+    return _result_dict(r, w)
+
+
+def solve_batch(models, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
+                node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None):
+    o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, threads, blocks)
+    n = len(models)
+    ws = [np.zeros(m.n_vars, dtype=np.int32) for m in models]
+    res = (_abi.pccp_result * n)()
+    for i in range(n):
+        res[i].witness = ws[i].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    rc = pccp_solve_batch([m.handle for m in models], o, res, _stream_ptr(stream))
+    check(rc, "pccp_solve_batch")
+    return [_result_dict(res[i], ws[i]) for i in range(n)]

@@ -1,0 +1,856 @@
+// pccp.cu -- kernels and C ABI of the PCCP propagate-and-search library (sm_103a).
+//
+// Kernels
+//   k_propagate   : persistent CTAs; the packed propagator table is brought
+//                   into shared memory once per CTA by TMA bulk copies; each
+//                   team of warps pulls stores from a global counter, stages
+//                   one store (joined with the root domains) into shared
+//                   memory and runs the lock-free fixed-point loop on it.
+//   k_solve       : one team per CTA walks one model's search tree depth first
+//                   in the sequential order (Sec. 5: propagate, branch, full
+//                   recomputation from the root store on backtrack); CTAs pull
+//                   models from a global counter, so a batch of uneven models
+//                   balances itself.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pccp.h"
+#include "pccp_device.cuh"
+
+using namespace pccp;
+
+namespace {
+
+constexpr int kDefaultMaxIter = 1 << 24;
+constexpr int kDefaultLinearMode = 1;  // a thread per linear row
+constexpr int kMaxTeamsPerCta = 15;  // named barriers 1..15
+constexpr int32_t kValueLimit = (1 << 30) - 1;
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ------------------------------------------------------------- propagation
+
+struct PropArgs {
+  const uint8_t* image;
+  const int2* root;
+  int32_t* lb;
+  int32_t* ub;
+  int32_t* status;
+  int32_t* iters;
+  int* counter;
+  uint32_t image_bytes;
+  int n_vars;
+  int n_stores;
+  int team_size;
+  int teams;
+  int max_iter;
+  int linear_mode;
+};
+
+__global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* img = smem;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + a.image_bytes);
+  int* ctrl_base = reinterpret_cast<int*>(smem + a.image_bytes + 16);
+  int2* st_base = reinterpret_cast<int2*>(smem + a.image_bytes + 16 + 16 * a.teams);
+
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  const bool ok = load_image(img, a.image, a.image_bytes, mbar, 0);
+
+  const int team_id = threadIdx.x / a.team_size;
+  Team tm;
+  tm.tid = threadIdx.x - team_id * a.team_size;
+  tm.nthr = a.team_size;
+  tm.bar = 1 + team_id;
+  tm.lane = threadIdx.x & 31;
+  tm.warp = tm.tid >> 5;
+  tm.nwarps = a.team_size >> 5;
+  int* ctrl = ctrl_base + 4 * team_id;  // [0] next store, [1] failure flag
+  int2* st = st_base + static_cast<size_t>(team_id) * a.n_vars;
+  const Tab tb = make_tab(img);
+  const int nv = a.n_vars;
+
+  for (;;) {
+    if (tm.tid == 0) ctrl[0] = atomicAdd(a.counter, 1);
+    team_bar(tm.bar, tm.nthr);
+    const int s = ctrl[0];
+    if (s >= a.n_stores) break;
+    if (!ok) {  // table never arrived: report the stores this team takes
+      if (tm.tid == 0) {
+        a.status[s] = kError;
+        if (a.iters) a.iters[s] = 0;
+      }
+      continue;
+    }
+    int32_t* lbs = a.lb + static_cast<size_t>(s) * nv;
+    int32_t* ubs = a.ub + static_cast<size_t>(s) * nv;
+    bool empty = false;
+    for (int v = tm.tid; v < nv; v += tm.nthr) {
+      const int2 r = __ldg(a.root + v);
+      const int l = max(lbs[v], r.x), u = min(ubs[v], r.y);
+      st[v] = make_int2(l, u);
+      empty |= l > u;
+    }
+    if (tm.tid == 0) ctrl[1] = 0;
+    const bool any_empty = team_bar_or(tm.bar, tm.nthr, empty);
+    int status = kFailed, it = 0;
+    if (!any_empty) status = team_fixpoint(tb, st, tm, &ctrl[1], a.max_iter, it, a.linear_mode);
+    for (int v = tm.tid; v < nv; v += tm.nthr) {
+      const int2 D = st[v];
+      lbs[v] = D.x;
+      ubs[v] = D.y;
+    }
+    if (tm.tid == 0) {
+      a.status[s] = status;
+      if (a.iters) a.iters[s] = it;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ search
+
+struct InstanceDesc {
+  const uint8_t* image;
+  const int2* root;
+  uint32_t image_bytes;
+  int32_t n_vars;
+  int32_t witness_off;
+  int32_t n_branch;
+  int32_t max_iter;
+  int32_t pad;
+};
+
+struct InstanceResult {
+  int32_t status, has_solution, objective, max_depth;
+  int64_t nodes, fails, solutions, iterations;
+  int32_t error, pad;
+};
+
+struct SolveArgs {
+  const InstanceDesc* inst;
+  InstanceResult* res;
+  int32_t* witness;
+  int2* stacks;  // [gridDim.x][max_depth]
+  int* counter;
+  int n_inst;
+  int max_depth;
+  int mode;
+  int strategy;
+  int obj_ub;
+  int linear_mode;
+  int64_t node_limit;
+  int64_t time_limit_ns;
+  uint32_t max_image_bytes;
+};
+
+// Broadcast slots of one team's search.  Each slot has one writer (thread 0)
+// and one write point per node; it is read right after the barrier that
+// follows the write and is not rewritten before another barrier has passed.
+struct SearchCtrl {
+  unsigned long long sel[2];  // selection key, one slot per node parity
+  int fail;    // fixed-point failure flag (reset in P1, set by any thread)
+  int stop;    // P1: limit reached
+  int record;  // solution path: copy the witness
+  int err;     // branch path: decision stack overflow
+  int depth;   // backtrack: new depth, -1 when the tree is exhausted
+  int next;    // next model index (CTA loop)
+  int pad[6];
+};
+
+constexpr unsigned long long kNoVar = ~0ull;
+constexpr uint32_t kRightBit = 0x80000000u;
+
+// Depth-first branch and bound of one model by one team (the whole CTA).
+// Each node's store is fix(root join decisions join objective bound); the
+// walk order is the sequential one: left child (ub <= m) subtree first.
+// All control decisions are made by thread 0 and broadcast through shared
+// memory; every broadcast slot is written before a barrier and read after it,
+// and never rewritten before the next barrier that follows all its reads.
+__device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st, const Team& tm,
+                         SearchCtrl* sc, int2* stack, const SolveArgs& a, int max_iter,
+                         int32_t* witness, InstanceResult* out) {
+  const int nv = tb.n_vars;
+  const uint64_t t0 = globaltimer_ns();
+  // thread-0 state
+  int64_t nodes = 0, fails = 0, sols = 0, iters = 0;
+  int depth = 0, max_d = 0, best = 0, objective = 0, error = 0;
+  bool has_sol = false, limited = false, satisfied = false;
+  unsigned par = 0;
+
+  for (int v = tm.tid; v < nv; v += tm.nthr) st[v] = __ldg(root + v);
+
+  for (;;) {
+    // P1: limits, objective bound, reset of per-node slots
+    if (tm.tid == 0) {
+      int stop = 0;
+      if (a.node_limit > 0 && nodes >= a.node_limit) stop = 1;
+      if (a.time_limit_ns > 0 && static_cast<int64_t>(globaltimer_ns() - t0) > a.time_limit_ns)
+        stop = 1;
+      if (!stop && tb.objective >= 0) {
+        int bound = a.obj_ub;
+        if (a.mode == PCCP_OPTIMISE && has_sol) bound = min(bound, best - 1);
+        if (bound < INT_MAX) atom_min_s32(&st[tb.objective].y, bound);
+      }
+      limited = stop != 0;
+      sc->stop = stop;
+      sc->fail = 0;
+      sc->sel[par] = kNoVar;
+    }
+    team_bar(tm.bar, tm.nthr);  // N1
+    if (sc->stop) break;
+    int it = 0;
+    const int fst = team_fixpoint(tb, st, tm, &sc->fail, max_iter, it, a.linear_mode);
+    if (tm.tid == 0) {
+      ++nodes;
+      iters += it;
+      max_d = max(max_d, depth);
+    }
+    if (fst == kError) {
+      if (tm.tid == 0) {
+        error = 1;
+        limited = true;
+      }
+      break;
+    }
+    bool backtrack = true;
+    if (fst == kFailed) {
+      if (tm.tid == 0) ++fails;
+    } else {
+      // A5: variable selection by a team-wide minimum over branch variables
+      unsigned long long* sel = &sc->sel[par];
+      for (int k = tm.tid; k < tb.n_branch; k += tm.nthr) {
+        const int v = tb.branch[k];
+        const int2 D = ld_dom(st, v);
+        if (D.x < D.y) {
+          unsigned long long key = static_cast<unsigned long long>(k);
+          if (a.strategy == PCCP_FIRST_FAIL)
+            key |= static_cast<unsigned long long>(static_cast<uint32_t>(D.y - D.x)) << 32;
+          atomicMin(sel, key);
+          if (a.strategy == PCCP_INPUT_ORDER) break;
+        }
+      }
+      team_bar(tm.bar, tm.nthr);  // N2
+      const unsigned long long key = *sel;
+      if (key == kNoVar) {  // every branch variable fixed: a solution
+        if (tm.tid == 0) {
+          ++sols;
+          const int z = tb.objective >= 0 ? st[tb.objective].x : 0;
+          const bool record = (a.mode == PCCP_OPTIMISE) || !has_sol;
+          if (record) {
+            best = z;
+            objective = z;
+          }
+          has_sol = true;
+          if (a.mode == PCCP_OPTIMISE && tb.objective < 0) satisfied = true;
+          sc->record = record;
+        }
+        team_bar(tm.bar, tm.nthr);  // N3
+        if (sc->record)
+          for (int v = tm.tid; v < nv; v += tm.nthr) witness[v] = st[v].x;
+      } else {
+        backtrack = false;
+        if (tm.tid == 0) {
+          const int v = tb.branch[static_cast<int>(key & 0xffffffffull)];
+          const int2 D = st[v];
+          const int m = D.x + (D.y - D.x) / 2;
+          if (depth >= a.max_depth) {
+            error = 2;
+          } else {
+            stack[depth] = make_int2(v, m);  // left: ub(v) <= m
+            ++depth;
+            atom_min_s32(&st[v].y, m);
+          }
+          sc->err = error != 0;
+        }
+        team_bar(tm.bar, tm.nthr);  // NB: publishes the error decision
+        if (sc->err) {
+          if (tm.tid == 0) limited = true;
+          break;
+        }
+      }
+    }
+    par ^= 1u;
+    if (backtrack) {
+      if (tm.tid == 0) {
+        while (depth > 0 && (static_cast<uint32_t>(stack[depth - 1].x) & kRightBit)) --depth;
+        if (depth == 0 || satisfied) {
+          sc->depth = -1;
+        } else {
+          const int2 e = stack[depth - 1];  // flip to the right child: lb(v) >= m + 1
+          stack[depth - 1] = make_int2(static_cast<int>(static_cast<uint32_t>(e.x) | kRightBit),
+                                       e.y + 1);
+          sc->depth = depth;
+        }
+      }
+      team_bar(tm.bar, tm.nthr);  // N4
+      const int d = sc->depth;
+      if (d < 0) break;
+      for (int v = tm.tid; v < nv; v += tm.nthr) st[v] = __ldg(root + v);
+      team_bar(tm.bar, tm.nthr);  // N5
+      for (int k = tm.tid; k < d; k += tm.nthr) {
+        const int2 e = stack[k];
+        const int v = static_cast<int>(static_cast<uint32_t>(e.x) & ~kRightBit);
+        if (static_cast<uint32_t>(e.x) & kRightBit)
+          atom_max_s32(&st[v].x, e.y);
+        else
+          atom_min_s32(&st[v].y, e.y);
+      }
+    }
+  }
+  if (tm.tid == 0) {
+    out->status = limited ? PCCP_RES_LIMIT : (has_sol ? PCCP_RES_OPTIMAL : PCCP_RES_INFEASIBLE);
+    out->has_solution = has_sol;
+    out->objective = has_sol ? objective : 0;
+    out->max_depth = max_d;
+    out->nodes = nodes;
+    out->fails = fails;
+    out->solutions = sols;
+    out->iterations = iters;
+    out->error = error;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* img = smem;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + a.max_image_bytes);
+  SearchCtrl* sc = reinterpret_cast<SearchCtrl*>(smem + a.max_image_bytes + 16);
+  int2* st = reinterpret_cast<int2*>(smem + a.max_image_bytes + 16 + sizeof(SearchCtrl));
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  Team tm;
+  tm.tid = threadIdx.x;
+  tm.nthr = blockDim.x;
+  tm.bar = 1;
+  tm.lane = threadIdx.x & 31;
+  tm.warp = threadIdx.x >> 5;
+  tm.nwarps = blockDim.x >> 5;
+  int2* stack = a.stacks + static_cast<size_t>(blockIdx.x) * a.max_depth;
+  uint32_t parity = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) sc->next = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int i = sc->next;
+    if (i >= a.n_inst) break;
+    const InstanceDesc d = a.inst[i];
+    if (!load_image(img, d.image, d.image_bytes, mbar, parity)) {
+      if (threadIdx.x == 0) {
+        a.res[i].status = PCCP_RES_LIMIT;
+        a.res[i].error = 3;
+      }
+      return;
+    }
+    parity ^= 1u;
+    const Tab tb = make_tab(img);
+    team_dfs(tb, d.root, st, tm, sc, stack, a, d.max_iter, a.witness + d.witness_off, &a.res[i]);
+  }
+}
+
+// -------------------------------------------------------------- host model
+
+struct Packed {
+  std::vector<uint8_t> image;  // header + sections, 16-byte aligned sizes
+  int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective;
+  int64_t bytes_per_sweep;
+};
+
+size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
+
+}  // namespace
+
+struct pccp_model {
+  int device;
+  int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective;
+  uint32_t image_bytes;
+  int64_t bytes_per_sweep;
+  int32_t max_iter;  // every changing iteration narrows some bound by >= 1
+  uint8_t* d_mem;    // image, then root int2[n_vars]
+  int2* d_root;
+};
+
+namespace {
+
+int64_t iabs64(int64_t x) { return x < 0 ? -x : x; }
+
+int validate_and_pack(const pccp_model_desc* d, Packed* p) {
+  if (!d) return PCCP_ERR_INVALID;
+  const int64_t nv = d->n_vars;
+  if (nv < 1) return PCCP_ERR_INVALID;
+  if (nv > 65535) return PCCP_ERR_UNSUPPORTED;
+  if (!d->lb0 || !d->ub0) return PCCP_ERR_INVALID;
+  std::vector<int64_t> B(nv);
+  for (int64_t v = 0; v < nv; ++v) {
+    if (d->lb0[v] > d->ub0[v]) return PCCP_ERR_INVALID;
+    if (d->lb0[v] < -kValueLimit || d->ub0[v] > kValueLimit) return PCCP_ERR_OVERFLOW;
+    B[v] = std::max(iabs64(d->lb0[v]), iabs64(d->ub0[v]));
+  }
+  auto in_range = [nv](int64_t v) { return v >= 0 && v < nv; };
+  if (d->n_temporal < 0 || d->n_linear < 0 || d->n_reified < 0 || d->n_branch < 0)
+    return PCCP_ERR_INVALID;
+  if (d->n_temporal > 0 && !d->temporal) return PCCP_ERR_INVALID;
+  if (d->n_reified > 0 && !d->reified) return PCCP_ERR_INVALID;
+  if (d->n_linear > 0 && (!d->linear_c || !d->linear_off)) return PCCP_ERR_INVALID;
+  if (d->n_branch > 0 && !d->branch_vars) return PCCP_ERR_INVALID;
+  if (d->objective < -1 || d->objective >= nv) return PCCP_ERR_INVALID;
+  for (int32_t k = 0; k < d->n_branch; ++k)
+    if (!in_range(d->branch_vars[k])) return PCCP_ERR_INVALID;
+
+  std::vector<uint2> T, RF;
+  std::vector<int4> L;
+  std::vector<uint32_t> TERMS;
+  int64_t bytes_per_sweep = 0;
+  for (int32_t i = 0; i < d->n_temporal; ++i) {
+    const int32_t x = d->temporal[3 * i], y = d->temporal[3 * i + 1], dd = d->temporal[3 * i + 2];
+    if (!in_range(x) || !in_range(y)) return PCCP_ERR_INVALID;
+    if (dd < -kValueLimit || dd > kValueLimit) return PCCP_ERR_OVERFLOW;
+    T.push_back(make_uint2(static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 16),
+                           static_cast<uint32_t>(dd)));
+    bytes_per_sweep += 20;
+  }
+  for (int32_t i = 0; i < d->n_reified; ++i) {
+    const int32_t b = d->reified[4 * i], x = d->reified[4 * i + 1], y = d->reified[4 * i + 2],
+                  dd = d->reified[4 * i + 3];
+    if (!in_range(b) || !in_range(x) || !in_range(y)) return PCCP_ERR_INVALID;
+    if (d->lb0[b] < 0 || d->ub0[b] > 1) return PCCP_ERR_INVALID;
+    if (dd < -32768 || dd > 32767) return PCCP_ERR_UNSUPPORTED;
+    RF.push_back(make_uint2(static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 16),
+                            static_cast<uint32_t>(b) |
+                                (static_cast<uint32_t>(static_cast<uint16_t>(dd)) << 16)));
+    bytes_per_sweep += 40;
+  }
+  if (d->n_linear > 0 && d->linear_off[0] != 0) return PCCP_ERR_INVALID;
+  for (int32_t i = 0; i < d->n_linear; ++i) {
+    const int32_t o0 = d->linear_off[i], o1 = d->linear_off[i + 1];
+    if (o1 < o0) return PCCP_ERR_INVALID;
+    if (o1 > o0 && (!d->term_coef || !d->term_var)) return PCCP_ERR_INVALID;
+    const int64_t c = d->linear_c[i];
+    int64_t sum = 0, mx = 0;
+    const int32_t first = static_cast<int32_t>(TERMS.size());
+    for (int32_t k = o0; k < o1; ++k) {
+      const int32_t a = d->term_coef[k], v = d->term_var[k];
+      if (!in_range(v)) return PCCP_ERR_INVALID;
+      if (a == 0) continue;
+      if (a < -32768 || a > 32767) return PCCP_ERR_UNSUPPORTED;
+      sum += iabs64(a) * B[v];
+      mx = std::max(mx, iabs64(a) * B[v]);
+      TERMS.push_back(static_cast<uint32_t>(v) |
+                      (static_cast<uint32_t>(static_cast<uint16_t>(a)) << 16));
+    }
+    const int32_t len = static_cast<int32_t>(TERMS.size()) - first;
+    if (len == 0) return PCCP_ERR_INVALID;
+    if (iabs64(c) + 2 * sum + 2 * mx > static_cast<int64_t>(INT32_MAX)) return PCCP_ERR_OVERFLOW;
+    L.push_back(make_int4(static_cast<int32_t>(c), first, len, 0));
+    bytes_per_sweep += 12 + 12 * static_cast<int64_t>(len);
+  }
+
+  TableHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.n_vars = static_cast<int32_t>(nv);
+  h.n_t = static_cast<int32_t>(T.size());
+  h.n_rf = static_cast<int32_t>(RF.size());
+  h.n_lin = static_cast<int32_t>(L.size());
+  h.n_terms = static_cast<int32_t>(TERMS.size());
+  h.n_branch = d->n_branch;
+  h.objective = d->objective;
+  size_t off = sizeof(TableHeader);
+  h.off_t = static_cast<int32_t>(off);
+  off = align16(off + T.size() * sizeof(uint2));
+  h.off_rf = static_cast<int32_t>(off);
+  off = align16(off + RF.size() * sizeof(uint2));
+  h.off_lin = static_cast<int32_t>(off);
+  off = align16(off + L.size() * sizeof(int4));
+  h.off_terms = static_cast<int32_t>(off);
+  off = align16(off + TERMS.size() * sizeof(uint32_t));
+  h.off_branch = static_cast<int32_t>(off);
+  off = align16(off + static_cast<size_t>(d->n_branch) * sizeof(int32_t));
+  if (off > (1u << 30)) return PCCP_ERR_UNSUPPORTED;
+  h.image_bytes = static_cast<int32_t>(off);
+
+  p->image.assign(off, 0);
+  std::memcpy(p->image.data(), &h, sizeof(h));
+  if (!T.empty()) std::memcpy(p->image.data() + h.off_t, T.data(), T.size() * sizeof(uint2));
+  if (!RF.empty()) std::memcpy(p->image.data() + h.off_rf, RF.data(), RF.size() * sizeof(uint2));
+  if (!L.empty()) std::memcpy(p->image.data() + h.off_lin, L.data(), L.size() * sizeof(int4));
+  if (!TERMS.empty())
+    std::memcpy(p->image.data() + h.off_terms, TERMS.data(), TERMS.size() * sizeof(uint32_t));
+  if (d->n_branch > 0)
+    std::memcpy(p->image.data() + h.off_branch, d->branch_vars,
+                static_cast<size_t>(d->n_branch) * sizeof(int32_t));
+  p->n_vars = h.n_vars;
+  p->n_t = h.n_t;
+  p->n_rf = h.n_rf;
+  p->n_lin = h.n_lin;
+  p->n_terms = h.n_terms;
+  p->n_branch = h.n_branch;
+  p->objective = h.objective;
+  p->bytes_per_sweep = bytes_per_sweep;
+  return PCCP_OK;
+}
+
+int max_dyn_smem() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return -1;
+  return v;
+}
+
+int sm_count() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  return v;
+}
+
+int check_device(const pccp_model* m) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PCCP_ERR_CUDA;
+  return dev == m->device ? PCCP_OK : PCCP_ERR_INVALID;
+}
+
+#define PCCP_CUDA(call)                    \
+  do {                                     \
+    if ((call) != cudaSuccess) {           \
+      (void)cudaGetLastError();            \
+      return PCCP_ERR_CUDA;                \
+    }                                      \
+  } while (0)
+
+struct PropPlan {
+  int team, teams, grid;
+  size_t smem;
+};
+
+int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_config* cfg,
+                   PropPlan* p) {
+  const int smem_max = max_dyn_smem();
+  const int sms = sm_count();
+  if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
+  int team = (cfg && cfg->team_threads > 0) ? cfg->team_threads : 128;
+  if (team % 32 != 0 || team > 1024) return PCCP_ERR_INVALID;
+  if (cfg && (cfg->linear_mode < 0 || cfg->linear_mode > 2)) return PCCP_ERR_INVALID;
+  const size_t base = static_cast<size_t>(m->image_bytes) + 16;
+  const size_t per_team = 16 + static_cast<size_t>(m->n_vars) * sizeof(int2);
+  if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
+  int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
+  int teams = (cfg && cfg->teams_per_cta > 0) ? cfg->teams_per_cta : 8;
+  if (teams > kMaxTeamsPerCta) return PCCP_ERR_INVALID;
+  teams = std::min({teams, fit, 1024 / team});
+  if (cfg && cfg->teams_per_cta > 0 && teams < cfg->teams_per_cta) return PCCP_ERR_SMEM;
+  if (teams < 1) return PCCP_ERR_SMEM;
+  const size_t smem = base + static_cast<size_t>(teams) * per_team;
+  if (cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return PCCP_ERR_CUDA;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate, teams * team, smem) !=
+      cudaSuccess) {
+    (void)cudaGetLastError();
+    return PCCP_ERR_CUDA;
+  }
+  if (per_sm < 1) return PCCP_ERR_SMEM;
+  if (cfg && cfg->ctas_per_sm > 0) per_sm = std::min(per_sm, static_cast<int>(cfg->ctas_per_sm));
+  const int want = (n_stores + teams - 1) / teams;
+  p->team = team;
+  p->teams = teams;
+  p->grid = std::max(1, std::min(want, sms * per_sm));
+  p->smem = smem;
+  return PCCP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pccp_error_string(int code) {
+  switch (code) {
+    case PCCP_OK: return "ok";
+    case PCCP_ERR_INVALID: return "invalid argument";
+    case PCCP_ERR_OVERFLOW: return "a propagator intermediate could overflow int32";
+    case PCCP_ERR_SMEM: return "model does not fit in shared memory";
+    case PCCP_ERR_TIMEOUT: return "a device wait or iteration budget ran out";
+    case PCCP_ERR_CUDA: return "CUDA runtime error";
+    case PCCP_ERR_UNSUPPORTED: return "model outside the packed-table limits";
+    default: return "unknown error";
+  }
+}
+
+int pccp_model_create(const pccp_model_desc* desc, pccp_model** out) {
+  if (!out) return PCCP_ERR_INVALID;
+  *out = nullptr;
+  Packed p;
+  const int rc = validate_and_pack(desc, &p);
+  if (rc != PCCP_OK) return rc;
+  int dev = 0;
+  PCCP_CUDA(cudaGetDevice(&dev));
+  pccp_model* m = new (std::nothrow) pccp_model;
+  if (!m) return PCCP_ERR_INVALID;
+  m->device = dev;
+  m->n_vars = p.n_vars;
+  m->n_t = p.n_t;
+  m->n_rf = p.n_rf;
+  m->n_lin = p.n_lin;
+  m->n_terms = p.n_terms;
+  m->n_branch = p.n_branch;
+  m->objective = p.objective;
+  m->image_bytes = static_cast<uint32_t>(p.image.size());
+  m->bytes_per_sweep = p.bytes_per_sweep;
+  {
+    // total width of the root box + 3 bounds the iterations of any store
+    int64_t w = 3;
+    for (int v = 0; v < p.n_vars; ++v) w += static_cast<int64_t>(desc->ub0[v]) - desc->lb0[v];
+    m->max_iter = static_cast<int32_t>(std::min<int64_t>(w, kDefaultMaxIter));
+  }
+  const size_t root_off = align16(p.image.size());
+  const size_t total = root_off + static_cast<size_t>(p.n_vars) * sizeof(int2);
+  std::vector<int2> root(p.n_vars);
+  for (int v = 0; v < p.n_vars; ++v) root[v] = make_int2(desc->lb0[v], desc->ub0[v]);
+  if (cudaMalloc(&m->d_mem, total) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete m;
+    return PCCP_ERR_CUDA;
+  }
+  m->d_root = reinterpret_cast<int2*>(m->d_mem + root_off);
+  if (cudaMemcpy(m->d_mem, p.image.data(), p.image.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_root, root.data(), root.size() * sizeof(int2), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaFree(m->d_mem);
+    delete m;
+    return PCCP_ERR_CUDA;
+  }
+  *out = m;
+  return PCCP_OK;
+}
+
+void pccp_model_destroy(pccp_model* m) {
+  if (!m) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  cudaFree(m->d_mem);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete m;
+}
+
+int pccp_model_get_info(const pccp_model* m, pccp_model_info* info) {
+  if (!m || !info) return PCCP_ERR_INVALID;
+  info->n_vars = m->n_vars;
+  info->n_temporal = m->n_t;
+  info->n_linear = m->n_lin;
+  info->n_terms = m->n_terms;
+  info->n_reified = m->n_rf;
+  info->table_bytes = static_cast<int32_t>(m->image_bytes);
+  info->bytes_per_sweep = m->bytes_per_sweep;
+  const int smem_max = max_dyn_smem();
+  int64_t room = static_cast<int64_t>(smem_max) - m->image_bytes - 32;
+  info->max_store_vars = room > 0 ? static_cast<int32_t>(std::min<int64_t>(room / 8, 65535)) : 0;
+  return PCCP_OK;
+}
+
+int pccp_propagate_ex(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_t* ub,
+                      int32_t* status, int32_t* iterations, const pccp_launch_config* cfg,
+                      void* stream) {
+  if (!m || n_stores < 0) return PCCP_ERR_INVALID;
+  if (n_stores == 0) return PCCP_OK;
+  if (!lb || !ub || !status) return PCCP_ERR_INVALID;
+  int rc = check_device(m);
+  if (rc != PCCP_OK) return rc;
+  PropPlan plan;
+  rc = plan_propagate(m, n_stores, cfg, &plan);
+  if (rc != PCCP_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* counter = nullptr;
+  PCCP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&counter), sizeof(int), s));
+  PCCP_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  PropArgs a;
+  a.image = m->d_mem;
+  a.root = m->d_root;
+  a.lb = lb;
+  a.ub = ub;
+  a.status = status;
+  a.iters = iterations;
+  a.counter = counter;
+  a.image_bytes = m->image_bytes;
+  a.n_vars = m->n_vars;
+  a.n_stores = n_stores;
+  a.team_size = plan.team;
+  a.teams = plan.teams;
+  a.max_iter = (cfg && cfg->max_iterations > 0) ? cfg->max_iterations : m->max_iter;
+  a.linear_mode = (cfg && cfg->linear_mode > 0) ? cfg->linear_mode - 1 : kDefaultLinearMode;
+  k_propagate<<<plan.grid, plan.team * plan.teams, plan.smem, s>>>(a);
+  const cudaError_t le = cudaGetLastError();
+  cudaFreeAsync(counter, s);
+  if (le != cudaSuccess) return PCCP_ERR_CUDA;
+  return PCCP_OK;
+}
+
+int pccp_propagate(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_t* ub,
+                   int32_t* status, int32_t* iterations, void* stream) {
+  return pccp_propagate_ex(m, n_stores, lb, ub, status, iterations, nullptr, stream);
+}
+
+int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
+                     const pccp_solve_opts* opts, pccp_result* results, void* stream) {
+  if (!models || n_models < 0 || !opts || !results) return PCCP_ERR_INVALID;
+  if (n_models == 0) return PCCP_OK;
+  if (opts->strategy != PCCP_INPUT_ORDER && opts->strategy != PCCP_FIRST_FAIL)
+    return PCCP_ERR_INVALID;
+  if (opts->mode != PCCP_OPTIMISE && opts->mode != PCCP_COUNT_ALL) return PCCP_ERR_INVALID;
+  const int smem_max = max_dyn_smem();
+  const int sms = sm_count();
+  if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
+  int threads = opts->threads > 0 ? opts->threads : 256;
+  if (threads % 32 != 0 || threads > 1024) return PCCP_ERR_INVALID;
+
+  std::vector<InstanceDesc> desc(n_models);
+  uint32_t max_img = 0;
+  int32_t max_vars = 0, max_branch = 0;
+  int64_t wit_total = 0;
+  for (int32_t i = 0; i < n_models; ++i) {
+    const pccp_model* m = models[i];
+    if (!m) return PCCP_ERR_INVALID;
+    const int rc = check_device(m);
+    if (rc != PCCP_OK) return rc;
+    desc[i].image = m->d_mem;
+    desc[i].root = m->d_root;
+    desc[i].image_bytes = m->image_bytes;
+    desc[i].n_vars = m->n_vars;
+    desc[i].n_branch = m->n_branch;
+    desc[i].witness_off = static_cast<int32_t>(wit_total);
+    desc[i].max_iter = m->max_iter;
+    wit_total += m->n_vars;
+    if (wit_total > INT32_MAX) return PCCP_ERR_INVALID;
+    max_img = std::max(max_img, m->image_bytes);
+    max_vars = std::max(max_vars, m->n_vars);
+    max_branch = std::max(max_branch, m->n_branch);
+  }
+  const size_t smem = static_cast<size_t>(max_img) + 16 + sizeof(SearchCtrl) +
+                      static_cast<size_t>(max_vars) * sizeof(int2);
+  if (smem > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
+  PCCP_CUDA(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem)));
+  int per_sm = 0;
+  PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, threads, smem));
+  if (per_sm < 1) return PCCP_ERR_SMEM;
+  int grid = std::min(n_models, sms * per_sm);
+  if (opts->blocks > 0) grid = std::min(grid, static_cast<int>(opts->blocks));
+  const int max_depth = 32 * std::max(max_branch, 1) + 2;
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // one scratch allocation: descriptors | results | witnesses | stacks | counter
+  const size_t o_desc = 0;
+  const size_t o_res = align16(o_desc + desc.size() * sizeof(InstanceDesc));
+  const size_t o_wit = align16(o_res + static_cast<size_t>(n_models) * sizeof(InstanceResult));
+  const size_t o_stk = align16(o_wit + static_cast<size_t>(wit_total) * sizeof(int32_t));
+  const size_t o_cnt =
+      align16(o_stk + static_cast<size_t>(grid) * max_depth * sizeof(int2));
+  const size_t total = o_cnt + 16;
+  uint8_t* dmem = nullptr;
+  PCCP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dmem), total, s));
+  int rc = PCCP_OK;
+  std::vector<InstanceResult> hres(n_models);
+  std::vector<int32_t> hwit(static_cast<size_t>(wit_total));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  do {
+    if (cudaMemcpyAsync(dmem + o_desc, desc.data(), desc.size() * sizeof(InstanceDesc),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(dmem + o_res, 0, static_cast<size_t>(n_models) * sizeof(InstanceResult),
+                        s) != cudaSuccess ||
+        cudaMemsetAsync(dmem + o_cnt, 0, 16, s) != cudaSuccess) {
+      rc = PCCP_ERR_CUDA;
+      break;
+    }
+    SolveArgs a;
+    a.inst = reinterpret_cast<const InstanceDesc*>(dmem + o_desc);
+    a.res = reinterpret_cast<InstanceResult*>(dmem + o_res);
+    a.witness = reinterpret_cast<int32_t*>(dmem + o_wit);
+    a.stacks = reinterpret_cast<int2*>(dmem + o_stk);
+    a.counter = reinterpret_cast<int*>(dmem + o_cnt);
+    a.n_inst = n_models;
+    a.max_depth = max_depth;
+    a.mode = opts->mode;
+    a.strategy = opts->strategy;
+    a.obj_ub = opts->obj_ub;
+    a.linear_mode = kDefaultLinearMode;
+    a.node_limit = opts->node_limit;
+    a.time_limit_ns = opts->time_limit_ms > 0 ? opts->time_limit_ms * 1000000ll : 0;
+    a.max_image_bytes = max_img;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      rc = PCCP_ERR_CUDA;
+      break;
+    }
+    cudaEventRecord(e0, s);
+    k_solve<<<grid, threads, smem, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) {
+      rc = PCCP_ERR_CUDA;
+      break;
+    }
+    cudaEventRecord(e1, s);
+    if (cudaMemcpyAsync(hres.data(), dmem + o_res,
+                        static_cast<size_t>(n_models) * sizeof(InstanceResult),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hwit.data(), dmem + o_wit, hwit.size() * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = PCCP_ERR_CUDA;
+      break;
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(dmem, s);
+  if (rc != PCCP_OK) {
+    (void)cudaGetLastError();
+    return rc;
+  }
+  for (int32_t i = 0; i < n_models; ++i) {
+    const InstanceResult& r = hres[i];
+    pccp_result& o = results[i];
+    o.status = r.status;
+    o.has_solution = r.has_solution;
+    o.objective = r.objective;
+    o.nodes = r.nodes;
+    o.fails = r.fails;
+    o.solutions = r.solutions;
+    o.iterations = r.iterations;
+    const pccp_model* m = models[i];
+    o.rows_evaluated = r.iterations * static_cast<int64_t>(m->n_t + m->n_rf + m->n_lin);
+    o.max_depth = r.max_depth;
+    o.elapsed_ms = ms;
+    if (o.witness && r.has_solution)
+      std::memcpy(o.witness, hwit.data() + desc[i].witness_off,
+                  static_cast<size_t>(m->n_vars) * sizeof(int32_t));
+    if (r.error == 1 || r.error == 3) rc = PCCP_ERR_TIMEOUT;
+    if (r.error == 2) rc = PCCP_ERR_INVALID;
+  }
+  return rc;
+}
+
+int pccp_solve(const pccp_model* m, const pccp_solve_opts* opts, pccp_result* result,
+               void* stream) {
+  if (!m || !opts || !result) return PCCP_ERR_INVALID;
+  if (!opts->deterministic) return PCCP_ERR_UNSUPPORTED;
+  pccp_solve_opts o = *opts;
+  if (o.threads <= 0) o.threads = 512;
+  const pccp_model* one[1] = {m};
+  return pccp_solve_batch(one, 1, &o, result, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,440 @@
+// pccp_device.cuh -- device-side building blocks of the propagation fixed point.
+//
+// A "team" is a group of whole warps (32..1024 threads) that owns one store of
+// intervals in shared memory and evaluates every propagator row of the model
+// on it, concurrently and without locks (Sec. 4 load/store semantics; Sec. 5
+// fixed-point loop).  Every tell is a lattice join done by an atomic max on a
+// lower bound or an atomic min on an upper bound (the join of ZInc / ZDec,
+// Sec. 2).  A tell is only issued when the candidate is strictly stronger
+// than the value the thread loaded (the "store only if ox > rx" rule of the
+// Sec. 4 compilation), and reads of shared bounds are relaxed atomic loads
+// (the ATOM requirement of Sec. 4 and the erratum of Sec. 5).  Teams
+// synchronise on a named barrier whose OR-reduction both ends an iteration
+// and detects the fixed point (the has_changed flags of Sec. 5).
+#pragma once
+
+#include <cstdint>
+
+namespace pccp {
+
+enum : int { kFixpoint = 0, kFailed = 1, kError = 2 };
+
+// Header at the start of the packed table image (64 bytes).  The image is
+// copied verbatim into shared memory, so every offset is relative to its start
+// and 16-byte aligned.
+struct TableHeader {
+  int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective, image_bytes;
+  int32_t off_t, off_rf, off_lin, off_terms, off_branch, pad0, pad1, pad2;
+};
+static_assert(sizeof(TableHeader) == 64, "header must be 64 bytes");
+
+// Row encodings (structure of arrays, one array per row kind):
+//   temporal  uint2 {x | y << 16, d}              x + d <= y
+//   reified   uint2 {x | y << 16, b | d << 16}    b <=> (x <= y && y < x + d), d int16
+//   linear    int4  {c, first term, len, 0}       sum coef*var <= c
+//   term      uint32 var | coef << 16             coef int16
+struct Tab {
+  const uint2* t;
+  const uint2* rf;
+  const int4* lin;
+  const uint32_t* terms;
+  const int32_t* branch;
+  int n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective;
+};
+
+__device__ __forceinline__ Tab make_tab(const uint8_t* img) {
+  const TableHeader* h = reinterpret_cast<const TableHeader*>(img);
+  Tab tb;
+  tb.n_vars = h->n_vars;
+  tb.n_t = h->n_t;
+  tb.n_rf = h->n_rf;
+  tb.n_lin = h->n_lin;
+  tb.n_terms = h->n_terms;
+  tb.n_branch = h->n_branch;
+  tb.objective = h->objective;
+  tb.t = reinterpret_cast<const uint2*>(img + h->off_t);
+  tb.rf = reinterpret_cast<const uint2*>(img + h->off_rf);
+  tb.lin = reinterpret_cast<const int4*>(img + h->off_lin);
+  tb.terms = reinterpret_cast<const uint32_t*>(img + h->off_terms);
+  tb.branch = reinterpret_cast<const int32_t*>(img + h->off_branch);
+  return tb;
+}
+
+// ------------------------------------------------------------ PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Relaxed, CTA-scope load of the interval {lb, ub} of variable v.  Each 32-bit
+// element is a single-copy-atomic access; lb and ub are independent lattice
+// components so they need not be read together.
+__device__ __forceinline__ int2 ld_dom(const int2* st, int v) {
+  int2 r;
+  asm volatile("ld.relaxed.cta.shared::cta.v2.s32 {%0, %1}, [%2];"
+               : "=r"(r.x), "=r"(r.y)
+               : "r"(smem_u32(st + v)));
+  return r;
+}
+
+__device__ __forceinline__ int atom_max_s32(int* p, int v) {
+  int old;
+  asm volatile("atom.relaxed.cta.shared::cta.max.s32 %0, [%1], %2;"
+               : "=r"(old)
+               : "r"(smem_u32(p)), "r"(v)
+               : "memory");
+  return old;
+}
+
+__device__ __forceinline__ int atom_min_s32(int* p, int v) {
+  int old;
+  asm volatile("atom.relaxed.cta.shared::cta.min.s32 %0, [%1], %2;"
+               : "=r"(old)
+               : "r"(smem_u32(p)), "r"(v)
+               : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void st_relaxed(int* p, int v) {
+  asm volatile("st.relaxed.cta.shared::cta.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.cta.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+
+// Named barrier over `n` threads (a multiple of 32) with an OR-reduction of p.
+__device__ __forceinline__ bool team_bar_or(int id, int n, bool p) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.s32 pi, %1, 0;\n\t"
+      "bar.red.or.pred po, %2, %3, pi;\n\t"
+      "selp.s32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<int>(p)), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void team_bar(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// ------------------------------------------------------------ team context
+
+struct Team {
+  int tid;     // thread index in the team
+  int nthr;    // team size (multiple of 32)
+  int bar;     // named barrier id (1..15)
+  int lane;
+  int warp;    // warp index in the team
+  int nwarps;
+};
+
+struct Flags {
+  bool ch;  // some tell strengthened the store
+  bool fl;  // some tell found an empty interval
+};
+
+// floor(a / b) for b > 0.
+__device__ __forceinline__ int floor_div_pos(int a, int b) {
+  int q = a / b;
+  if ((a % b != 0) && (a < 0)) --q;
+  return q;
+}
+
+// Join cand into lb(v).  lb_seen/ub_seen are the values this thread loaded;
+// bounds only move inward, so cand <= lb_seen means the tell is a no-op and
+// cand > ub_seen means the interval is empty whatever happened since.
+__device__ __forceinline__ void tell_lb(int2* st, int v, int cand, int lb_seen, int ub_seen,
+                                        Flags& f) {
+  if (cand <= lb_seen) return;
+  if (cand > ub_seen) {
+    f.fl = true;
+    return;
+  }
+  int old = atom_max_s32(&st[v].x, cand);
+  if (old < cand) f.ch = true;
+}
+
+__device__ __forceinline__ void tell_ub(int2* st, int v, int cand, int lb_seen, int ub_seen,
+                                        Flags& f) {
+  if (cand >= ub_seen) return;
+  if (cand < lb_seen) {
+    f.fl = true;
+    return;
+  }
+  int old = atom_min_s32(&st[v].y, cand);
+  if (old > cand) f.ch = true;
+}
+
+// Temporal row x + d <= y: ub(x) <= ub(y) - d and lb(y) >= lb(x) + d
+// (the [[x + y <= c]] compilation of Sec. 2 with y negated).  The common case
+// (nothing to tell) costs one branch.
+__device__ __forceinline__ void eval_temporal(uint2 row, int2* st, Flags& f) {
+  const int x = row.x & 0xffff, y = row.x >> 16, d = static_cast<int>(row.y);
+  const int2 X = ld_dom(st, x), Y = ld_dom(st, y);
+  const int cux = Y.y - d, cly = X.x + d;
+  if (cux < X.y || cly > Y.x) {
+    tell_ub(st, x, cux, X.x, X.y, f);
+    tell_lb(st, y, cly, Y.x, Y.y, f);
+  }
+}
+
+// Reified row b <=> (A and B), A: x <= y, B: y <= x + d - 1: the four asks of
+// [[phi <=> psi]] (Sec. 2) evaluated on one snapshot; the candidates of every
+// ask are joined per bound with selects, and the tells (rare once the store
+// settles) sit behind one branch.
+__device__ __forceinline__ void eval_reified(uint2 row, int2* st, Flags& f) {
+  const int x = row.x & 0xffff, y = row.x >> 16;
+  const int b = row.y & 0xffff, d = static_cast<int>(row.y) >> 16;
+  const int2 X = ld_dom(st, x), Y = ld_dom(st, y), B = ld_dom(st, b);
+  const bool entA = X.y <= Y.x;           // ub x <= lb y
+  const bool entB = Y.y <= X.x + d - 1;   // ub y <= lb x + d - 1
+  const bool entNA = X.x >= Y.y + 1;      // lb x >= ub y + 1
+  const bool entNB = Y.x >= X.y + d;      // lb y >= ub x + d
+  const bool bt = B.x >= 1;               // b entailed: tell A and B
+  const bool bfA = B.y <= 0 && entA;      // not b, A holds: tell not B (x + d <= y)
+  const bool bfB = B.y <= 0 && entB;      // not b, B holds: tell not A (y + 1 <= x)
+  int nux = X.y, nlx = X.x, nuy = Y.y, nly = Y.x;
+  if (bt) {
+    nux = min(nux, Y.y);
+    nly = max(nly, X.x);
+    nuy = min(nuy, X.y + d - 1);
+    nlx = max(nlx, Y.x - d + 1);
+  }
+  if (bfA) {
+    nly = max(nly, X.x + d);
+    nux = min(nux, Y.y - d);
+  }
+  if (bfB) {
+    nlx = max(nlx, Y.x + 1);
+    nuy = min(nuy, X.y - 1);
+  }
+  const int nlb = (entA && entB) ? max(B.x, 1) : B.x;    // A and B entailed: b
+  const int nub = (entNA || entNB) ? min(B.y, 0) : B.y;  // not (A and B) entailed: not b
+  if (nlx > X.x || nux < X.y || nly > Y.x || nuy < Y.y || nlb > B.x || nub < B.y) {
+    tell_lb(st, x, nlx, X.x, X.y, f);
+    tell_ub(st, x, nux, X.x, X.y, f);
+    tell_lb(st, y, nly, Y.x, Y.y, f);
+    tell_ub(st, y, nuy, Y.x, Y.y, f);
+    tell_lb(st, b, nlb, B.x, B.y, f);
+    tell_ub(st, b, nub, B.x, B.y, f);
+  }
+}
+
+// Linear row sum a_k x_k <= c, one warp per row, lanes over terms.  S is the
+// minimum of the whole sum over the box; term k may be bounded by
+// slack_k = c - (S - min_k).  If S + (largest span of one term) <= c no term
+// can move, so the second pass is skipped.  Terms of the first 32 stay in
+// registers; longer rows reload theirs (a fresher bound only weakens the
+// tell, which stays sound, and the last iteration sees a stable store).
+__device__ __forceinline__ void eval_linear_warp(const Tab& tb, int r, int lane, int2* st,
+                                                 Flags& f) {
+  const int4 h = tb.lin[r];
+  const int c = h.x, off = h.y, len = h.z;
+  int S = 0, span = 0;
+  int v0 = 0, a0 = 0;
+  int2 D0 = make_int2(0, 0);
+  for (int k = lane; k < len; k += 32) {
+    const uint32_t t = tb.terms[off + k];
+    const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
+    const int2 D = ld_dom(st, v);
+    const int mt = a > 0 ? a * D.x : a * D.y;
+    const int sp = a > 0 ? a * (D.y - D.x) : a * (D.x - D.y);
+    S += mt;
+    span = max(span, sp);
+    if (k < 32) {
+      v0 = v;
+      a0 = a;
+      D0 = D;
+    }
+  }
+  S = __reduce_add_sync(0xffffffffu, S);
+  span = __reduce_max_sync(0xffffffffu, span);
+  if (S > c) {  // even the smallest sum exceeds c
+    f.fl = true;
+    return;
+  }
+  if (S + span <= c) return;
+  for (int k = lane; k < len; k += 32) {
+    int v, a;
+    int2 D;
+    if (k < 32) {
+      v = v0;
+      a = a0;
+      D = D0;
+    } else {
+      const uint32_t t = tb.terms[off + k];
+      v = t & 0xffff;
+      a = static_cast<int>(t) >> 16;
+      D = ld_dom(st, v);
+    }
+    const int mt = a > 0 ? a * D.x : a * D.y;
+    const int slack = c - (S - mt);
+    if (a > 0) {
+      if (a * D.y > slack) tell_ub(st, v, floor_div_pos(slack, a), D.x, D.y, f);
+    } else {
+      // a x <= slack with a < 0: x >= ceil(slack / a) = -floor(slack / -a)
+      if (a * D.x > slack) tell_lb(st, v, -floor_div_pos(slack, -a), D.x, D.y, f);
+    }
+  }
+}
+
+// Linear row sum a_k x_k <= c evaluated by one thread: the same two passes
+// as eval_linear_warp with the sum kept in a register (no warp reduction and
+// no idle lanes on rows shorter than a warp).
+__device__ __forceinline__ void eval_linear_thread(const Tab& tb, int r, int2* st, Flags& f) {
+  const int4 h = tb.lin[r];
+  const int c = h.x, off = h.y, len = h.z;
+  int S = 0, span = 0;
+#pragma unroll 4
+  for (int k = 0; k < len; ++k) {
+    const uint32_t t = tb.terms[off + k];
+    const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
+    const int2 D = ld_dom(st, v);
+    S += a > 0 ? a * D.x : a * D.y;
+    span = max(span, a > 0 ? a * (D.y - D.x) : a * (D.x - D.y));
+  }
+  if (S > c) {
+    f.fl = true;
+    return;
+  }
+  if (S + span <= c) return;
+  for (int k = 0; k < len; ++k) {
+    const uint32_t t = tb.terms[off + k];
+    const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
+    const int2 D = ld_dom(st, v);
+    const int mt = a > 0 ? a * D.x : a * D.y;
+    const int slack = c - (S - mt);
+    if (a > 0) {
+      if (a * D.y > slack) tell_ub(st, v, floor_div_pos(slack, a), D.x, D.y, f);
+    } else {
+      if (a * D.x > slack) tell_lb(st, v, -floor_div_pos(slack, -a), D.x, D.y, f);
+    }
+  }
+}
+
+// One full evaluation of every row of the table (one iteration of the
+// eventless loop).  Rows of one kind run back to back so warps stay uniform.
+// linear_mode 0: a warp per linear row; 1: a thread per linear row.
+__device__ __forceinline__ void sweep_rows(const Tab& tb, int2* st, const Team& tm, Flags& f,
+                                           int linear_mode) {
+  for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified(tb.rf[r], st, f);
+  for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal(tb.t[r], st, f);
+  if (linear_mode == 1) {
+    for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) eval_linear_thread(tb, r, st, f);
+  } else {
+    for (int r = tm.warp; r < tb.n_lin; r += tm.nwarps) eval_linear_warp(tb, r, tm.lane, st, f);
+  }
+}
+
+// Fixed-point loop of one team on its store `st` (Sec. 5): iterate until an
+// iteration changes nothing or some tell finds an empty interval.  Failure is
+// checked inside the loop (an infeasible cycle would otherwise keep raising
+// bounds); when the loop goes quiet a final scan catches an interval emptied
+// by two concurrent tells that each saw a stale opposite bound.
+// Preconditions: st staged and published to the team by a barrier; *fail == 0
+// and published.  The caller must not modify *fail before the next team
+// barrier after this returns.  Team-uniform return value.
+__device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team& tm, int* fail,
+                                             int max_iter, int& iters, int linear_mode) {
+  int it = 0;
+  for (;;) {
+    Flags f{false, false};
+    sweep_rows(tb, st, tm, f, linear_mode);
+    if (f.fl) st_relaxed(fail, 1);
+    ++it;
+    const bool any = team_bar_or(tm.bar, tm.nthr, f.ch || f.fl);
+    if (ld_relaxed(fail)) {
+      iters = it;
+      return kFailed;
+    }
+    if (!any) break;
+    if (it >= max_iter) {
+      iters = it;
+      return kError;
+    }
+  }
+  bool empty = false;
+  for (int v = tm.tid; v < tb.n_vars; v += tm.nthr) {
+    const int2 D = ld_dom(st, v);
+    empty |= D.x > D.y;
+  }
+  iters = it;
+  return team_bar_or(tm.bar, tm.nthr, empty) ? kFailed : kFixpoint;
+}
+
+// ------------------------------------------------ bulk copy of the table image
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1-D TMA bulk copy global -> shared, completing `bytes` on the mbarrier.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: true when the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity, int max_tries) {
+  for (int i = 0; i < max_tries; ++i)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
+}
+
+// Copy the table image into shared memory with TMA bulk copies issued by
+// thread 0 of the CTA; every thread waits (bounded) for completion.  Must be
+// called by all threads of the CTA.  `parity` is the mbarrier phase to wait
+// for (flip it after each use).  Returns false if the wait gave up; then the
+// caller must not read the image.
+__device__ __forceinline__ bool load_image(uint8_t* dst, const uint8_t* src, uint32_t bytes,
+                                           uint64_t* mbar, uint32_t parity) {
+  __syncthreads();  // earlier generic-proxy reads of dst are done
+  if (threadIdx.x == 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(mbar, bytes);
+    const uint32_t chunk = 32768;
+    for (uint32_t o = 0; o < bytes; o += chunk) {
+      const uint32_t n = (bytes - o < chunk) ? (bytes - o) : chunk;
+      bulk_copy_g2s(dst + o, src + o, n, mbar);
+    }
+  }
+  bool ok = mbar_wait_bounded(mbar, parity, 1 << 22);
+  if (!ok) ok = mbar_wait_bounded(mbar, parity, 1 << 22);  // drain before giving up
+  return __syncthreads_and(ok) != 0;
+}
+
+}  // namespace pccp

@@ -33,10 +33,9 @@ def draw_generic_model(seed: int, n_int: int = 6, n_bool: int = 4, dom: int = 12
     nv = n_int + n_bool
     lb0, ub0 = [], []
     for _ in range(n_int):
-        a = g.uniform_int(-dom, dom)
-        b = g.uniform_int(-dom, dom)
-        lb0.append(min(a, b))
-        ub0.append(max(a, b))
+        a = g.uniform_int(-dom, dom // 2)
+        lb0.append(a)
+        ub0.append(a + g.uniform_int(0, 2 * dom))
     for _ in range(n_bool):
         lb0.append(0)
         ub0.append(1)
@@ -44,7 +43,16 @@ def draw_generic_model(seed: int, n_int: int = 6, n_bool: int = 4, dom: int = 12
     for _ in range(n_temporal):
         x = g.uniform_int(0, n_int - 1)
         y = g.uniform_int(0, n_int - 1)
-        d = g.uniform_int(-3 if allow_negative else 0, 6)
+        if n_int > 1 and g.uniform_int(0, 7) != 0:  # mostly distinct variables
+            while y == x:
+                y = g.uniform_int(0, n_int - 1)
+        if x > y and g.uniform_int(0, 3) != 0:  # mostly lower -> higher index
+            x, y = y, x
+        d = g.uniform_int(-4 if allow_negative else 0, 4)
+        if x > y and allow_negative:  # backward rows mostly slack: feasible cycles
+            d = -g.uniform_int(0, 2 * dom)
+        if x == y:  # x + d <= x holds iff d <= 0; keep the degenerate row satisfiable
+            d = -g.uniform_int(0, 3)
         temporal.append((x, y, d))
     linear = []
     for _ in range(n_linear):
@@ -56,7 +64,7 @@ def draw_generic_model(seed: int, n_int: int = 6, n_bool: int = 4, dom: int = 12
             if a == 0:
                 a = 1
             vs.append((a, v))
-        c = g.uniform_int(-dom, 2 * dom)
+        c = g.uniform_int(-dom, 3 * dom * coef)
         linear.append((c, vs))
     reified = []
     for _ in range(n_reified if n_bool > 0 else 0):
@@ -69,7 +77,7 @@ def draw_generic_model(seed: int, n_int: int = 6, n_bool: int = 4, dom: int = 12
                         branch=list(range(n_int)))
 
 
-def draw_generic_store(model: GenericModel, seed: int, p_narrow: float = 0.5):
+def draw_generic_store(model: GenericModel, seed: int, p_narrow: float = 0.3):
     """A random store inside the model's domains (each bound narrowed with
     probability p_narrow); may be empty nowhere."""
     g = SplitMix64.derive(seed, 0x570E)

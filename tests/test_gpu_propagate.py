@@ -1,0 +1,155 @@
+"""GPU parity of pccp_propagate (through the C ABI) with the CPU oracle:
+bit-exact lb/ub on every store that reaches a fixed point, equal status on
+every store (the fixed point is unique for any fair order: Theorem 1 and the
+fix D = fix O theorem; the load/store soundness and completeness theorems
+carry it to the lock-free GPU execution)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.rcpsp import rcpsp_model, node_store
+import paper_2207_12116_gb300 as pccp
+from synthetic import (config_instance, draw_generic_model, draw_generic_store,
+                       draw_partial_assignments, SplitMix64)
+from tests.gpu_util import compare_batch, oracle_model_from_lists
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def run(model, lb, ub, cfg=None):
+    dlb = torch.from_numpy(np.ascontiguousarray(lb, dtype=np.int32)).cuda()
+    dub = torch.from_numpy(np.ascontiguousarray(ub, dtype=np.int32)).cuda()
+    st, it = pccp.propagate(model, dlb, dub, config=cfg)
+    torch.cuda.synchronize()
+    return st.cpu().numpy(), dlb.cpu().numpy(), dub.cpu().numpy(), it.cpu().numpy()
+
+
+def generic_batch(seed, n_stores, **kw):
+    gm = draw_generic_model(seed, **kw)
+    m = pccp.Model.from_lists(gm.lb0, gm.ub0, gm.temporal, gm.linear, gm.reified,
+                              gm.objective, gm.branch)
+    lbs, ubs = [], []
+    for k in range(n_stores):
+        lb, ub = draw_generic_store(gm, seed * 1000 + k)
+        lbs.append(lb)
+        ubs.append(ub)
+    return gm, m, np.array(lbs), np.array(ubs)
+
+
+CONFIGS = [None,
+           pccp.launch_config(32, 1),
+           pccp.launch_config(64, 4, linear_mode=1),
+           pccp.launch_config(64, 4, linear_mode=2),
+           pccp.launch_config(256, 2, linear_mode=1),
+           pccp.launch_config(1024, 1, linear_mode=2),
+           pccp.launch_config(96, 10, 1)]
+
+
+@pytest.mark.parametrize("cfg_i", range(len(CONFIGS)))
+def test_generic_models_bit_exact(cfg_i):
+    tot_x = tot_f = 0
+    for seed in range(60):
+        gm, m, lb, ub = generic_batch(seed, 24)
+        st, glb, gub, _ = run(m, lb, ub, CONFIGS[cfg_i])
+        x, f = compare_batch(oracle_model_from_lists(gm), lb, ub, st, glb, gub)
+        tot_x += x
+        tot_f += f
+    assert tot_x > 100 and tot_f > 100
+
+
+def test_long_linear_rows_and_wide_domains():
+    """Rows longer than a warp (the reload path), large coefficients."""
+    tot_x = 0
+    for seed in range(40):
+        gm, m, lb, ub = generic_batch(10_000 + seed, 16, n_int=40, n_bool=40, dom=300,
+                                      n_temporal=4, n_linear=6, n_reified=8, max_len=100,
+                                      coef=30)
+        st, glb, gub, _ = run(m, lb, ub)
+        x, _ = compare_batch(oracle_model_from_lists(gm), lb, ub, st, glb, gub)
+        tot_x += x
+    assert tot_x > 20
+
+
+def test_j30_nodes_bit_exact():
+    inst = config_instance("j30", 0)
+    m = pccp.Model.from_rcpsp(inst)
+    om = rcpsp_model(inst)
+    nodes = draw_partial_assignments(inst.n, inst.horizon, 1500, seed=1)
+    rows = pccp.rcpsp.build_rows(inst)
+    lb, ub = pccp.rcpsp.node_stores(rows, nodes)
+    olb = np.array([node_store(om, d)[0] for d in nodes])
+    oub = np.array([node_store(om, d)[1] for d in nodes])
+    assert np.array_equal(olb, lb) and np.array_equal(oub, ub)  # same inputs both sides
+    st, glb, gub, it = run(m, lb, ub)
+    x, f = compare_batch(om, lb, ub, st, glb, gub)
+    assert x > 100 and f > 100
+    assert (it[st == 0] >= 1).all()
+
+
+def test_uneven_models_bit_exact():
+    for seed in range(6):
+        inst = config_instance("mixed30_60", seed)
+        m = pccp.Model.from_rcpsp(inst)
+        om = rcpsp_model(inst)
+        nodes = draw_partial_assignments(inst.n, inst.horizon, 150, seed=100 + seed)
+        lb, ub = pccp.rcpsp.node_stores(pccp.rcpsp.build_rows(inst), nodes)
+        st, glb, gub, _ = run(m, lb, ub)
+        compare_batch(om, lb, ub, st, glb, gub)
+
+
+def test_full_size_batch_sampled():
+    """The 10,000-node j30 batch in the default launch shape: a sample checked
+    store by store against the oracle, every store checked for properties
+    that hold at any size (re-propagating a fixed point changes nothing and
+    takes one iteration; results lie inside the input box)."""
+    inst = config_instance("j30", 0)
+    m = pccp.Model.from_rcpsp(inst)
+    om = rcpsp_model(inst)
+    nodes = draw_partial_assignments(inst.n, inst.horizon, 10_000, seed=1)
+    lb, ub = pccp.rcpsp.node_stores(pccp.rcpsp.build_rows(inst), nodes)
+    st, glb, gub, it = run(m, lb, ub)
+    g = SplitMix64(2024)
+    sample = sorted({g.uniform_int(0, 9_999) for _ in range(300)} | {0, 9_999})
+    compare_batch(om, lb, ub, st, glb, gub, rows=sample)
+    ok = st == pccp.PCCP_FIXPOINT
+    assert set(np.unique(st)) <= {0, 1}
+    assert (glb[ok] >= lb[ok]).all() and (gub[ok] <= ub[ok]).all()
+    st2, glb2, gub2, it2 = run(m, glb[ok], gub[ok])
+    assert (st2 == 0).all() and (it2 == 1).all()
+    assert np.array_equal(glb2, glb[ok]) and np.array_equal(gub2, gub[ok])
+
+
+def test_launch_shapes_agree():
+    gm, m, lb, ub = generic_batch(77, 200, n_int=12, n_bool=12, n_temporal=12, n_linear=5,
+                                  n_reified=12, max_len=8)
+    ref = run(m, lb, ub)
+    for cfg in CONFIGS[1:]:
+        out = run(m, lb, ub, cfg)
+        ok = ref[0] == 0
+        assert np.array_equal(out[0], ref[0])
+        assert np.array_equal(out[1][ok], ref[1][ok]) and np.array_equal(out[2][ok], ref[2][ok])
+
+
+def test_edge_cases():
+    # no rows at all: the result is the input joined with the root
+    m = pccp.Model([0, -3], [9, 3])
+    st, glb, gub, it = run(m, np.array([[2, -9], [5, 0]]), np.array([[20, 9], [4, 0]]))
+    assert st.tolist() == [0, 1]
+    assert glb[0].tolist() == [2, -3] and gub[0].tolist() == [9, 3]
+    # zero stores queue nothing
+    e = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    st0, _ = pccp.propagate(m, e, e.clone())
+    assert st0.numel() == 0
+    # an infeasible cycle x + 1 <= y, y + 1 <= x must end in failure
+    cyc = pccp.Model.from_lists([0, 0], [1000, 1000], temporal=[(0, 1, 1), (1, 0, 1)])
+    st, _, _, it = run(cyc, np.array([[0, 0]]), np.array([[1000, 1000]]))
+    assert st.tolist() == [1] and it[0] >= 1
+    # one store, one variable, a linear row fixing it
+    one = pccp.Model.from_lists([0], [10], linear=[(7, [(2, 0)])])
+    st, glb, gub, _ = run(one, np.array([[0]]), np.array([[10]]))
+    assert st.tolist() == [0] and gub[0].tolist() == [3]
+    # an iteration budget of 1 on a store that needs more reports PCCP_ERROR
+    chain = pccp.Model.from_lists([0] * 6, [50] * 6, temporal=[(i, i + 1, 2) for i in range(5)])
+    st, *_ = run(chain, np.zeros((1, 6)), np.full((1, 6), 50), pccp.launch_config(32, 1, 0, 1))
+    assert st.tolist() == [pccp.PCCP_ERROR]

@@ -1,0 +1,77 @@
+"""GPU parity of pccp_solve / pccp_solve_batch with the oracle's depth-first
+branch and bound: in the deterministic order the optimum, the witness and
+the node, failure and solution counts are equal."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.rcpsp import rcpsp_model
+import paper_2207_12116_gb300 as pccp
+from synthetic import config_instance, draw_generic_model
+from tests.gpu_util import oracle_model_from_lists
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STATUS = {oracle.RES_OPTIMAL: pccp.PCCP_RES_OPTIMAL, oracle.RES_INFEASIBLE: pccp.PCCP_RES_INFEASIBLE,
+          oracle.RES_LIMIT: pccp.PCCP_RES_LIMIT}
+
+
+def same(r, o):
+    assert r["status"] == STATUS[o["status"]], (r, o)
+    assert (r["nodes"], r["fails"], r["solutions"]) == (o["nodes"], o["fails"], o["solutions"]), (r, o)
+    assert r["has_solution"] == o["has_solution"]
+    if o["has_solution"]:
+        assert r["objective"] == o["objective"]
+        assert np.array_equal(r["witness"], o["witness"])
+    assert r["max_depth"] == o["max_depth"]
+
+
+def test_tiny8_single_solves():
+    for seed in range(0, 100, 5):
+        inst = config_instance("tiny8", seed)
+        same(pccp.solve(pccp.Model.from_rcpsp(inst)), oracle.solve(rcpsp_model(inst)))
+
+
+def test_tiny8_batch_one_launch():
+    insts = [config_instance("tiny8", s) for s in range(100)]
+    res = pccp.solve_batch([pccp.Model.from_rcpsp(i) for i in insts])
+    for inst, r in zip(insts, res):
+        same(r, oracle.solve(rcpsp_model(inst)))
+
+
+@pytest.mark.parametrize("threads", [32, 128, 1024])
+def test_tiny8_first_fail_and_team_sizes(threads):
+    for seed in range(0, 100, 9):
+        inst = config_instance("tiny8", seed)
+        r = pccp.solve(pccp.Model.from_rcpsp(inst), strategy=pccp.PCCP_FIRST_FAIL, threads=threads)
+        same(r, oracle.solve(rcpsp_model(inst), strategy=oracle.FIRST_FAIL))
+
+
+def test_tiny8_count_all_under_optimum():
+    for seed in range(0, 100, 10):
+        inst = config_instance("tiny8", seed)
+        o = oracle.solve(rcpsp_model(inst))
+        c = oracle.solve(rcpsp_model(inst), mode=oracle.COUNT_ALL, obj_ub=o["objective"])
+        r = pccp.solve(pccp.Model.from_rcpsp(inst), mode=pccp.PCCP_COUNT_ALL, obj_ub=o["objective"])
+        same(r, c)
+        assert r["solutions"] >= 1
+
+
+def test_node_limited_j30_and_mixed_batch():
+    insts = [config_instance("j30", s) for s in range(4)] + \
+            [config_instance("mixed30_60", s) for s in range(12)]
+    res = pccp.solve_batch([pccp.Model.from_rcpsp(i) for i in insts], node_limit=400)
+    for inst, r in zip(insts, res):
+        o = oracle.solve(rcpsp_model(inst), node_limit=400)
+        same(r, o)
+
+
+def test_generic_models_search():
+    for seed in range(40):
+        gm = draw_generic_model(9000 + seed, n_int=4, n_bool=3, dom=6)
+        m = pccp.Model.from_lists(gm.lb0, gm.ub0, gm.temporal, gm.linear, gm.reified,
+                                  gm.objective, gm.branch)
+        om = oracle_model_from_lists(gm)
+        same(pccp.solve(m), oracle.solve(om))
+        same(pccp.solve(m, mode=pccp.PCCP_COUNT_ALL), oracle.solve(om, mode=oracle.COUNT_ALL))
