@@ -43,6 +43,8 @@ extern "C" {
 #define PCCP_ERR_CUDA (-5)     /* a CUDA runtime call failed */
 #define PCCP_ERR_UNSUPPORTED (-6) /* valid model outside this build's packed limits
                                      (> 65535 variables, |coef| > 32767, ...) */
+#define PCCP_ERR_SCRATCH (-7)  /* request larger than the fixed scratch of the
+                                  allocation-free entry point */
 
 /* ---- per-store status written by pccp_propagate ------------------------ */
 #define PCCP_FIXPOINT 0 /* lb/ub hold the least fixed point */
@@ -212,6 +214,30 @@ int pccp_solve(const pccp_model* model, const pccp_solve_opts* opts, pccp_result
  * Errors: INVALID, SMEM, TIMEOUT, CUDA. */
 int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
                      const pccp_solve_opts* opts, pccp_result* results, void* stream);
+
+/* ---- allocation-free batched solve ------------------------------------- */
+
+/* No counterpart in the paper.  Same contract and results as
+ * pccp_solve_batch, for callers that may not allocate device memory (hosts
+ * that reserve all memory at start-up, plug-ins whose application owns the
+ * allocator, work issued while a stream is being captured): this call makes no
+ * cudaMalloc / cudaFree / memory-pool call of any kind.
+ * Its scratch (model descriptors, results, witnesses, decision stacks, work
+ * counter) is one fixed array of PCCP_NOALLOC_SCRATCH_BYTES in the library's
+ * device memory; every GPU that loads the library holds it until the process
+ * exits.  A request whose scratch does not fit returns PCCP_ERR_SCRATCH before
+ * anything is queued: descriptors 40 B + results 56 B per model, 4 B per
+ * variable of every model, and at least one decision stack of
+ * (32 x max branch variables + 2) x 8 B.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * on a device share the array, so calls that overlap on the GPU race:
+ * serialise them (for instance on one stream).  results[i].elapsed_ms is the
+ * host wall time of the whole call.  Errors: INVALID, SCRATCH, SMEM,
+ * TIMEOUT, CUDA. */
+#define PCCP_NOALLOC_SCRATCH_BYTES (8u << 20)
+int pccp_solve_batch_noalloc(const pccp_model* const* models, int32_t n_models,
+                             const pccp_solve_opts* opts, pccp_result* results, void* stream);
 
 /* Human-readable name of a return code (static storage). */
 const char* pccp_error_string(int code);

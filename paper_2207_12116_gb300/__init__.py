@@ -15,7 +15,8 @@ import numpy as np
 
 from . import _abi
 from ._abi import (PCCP_OK, PCCP_ERR_INVALID, PCCP_ERR_OVERFLOW, PCCP_ERR_SMEM,  # noqa: F401
-                   PCCP_ERR_TIMEOUT, PCCP_ERR_CUDA, PCCP_ERR_UNSUPPORTED, PCCP_FIXPOINT,
+                   PCCP_ERR_TIMEOUT, PCCP_ERR_CUDA, PCCP_ERR_UNSUPPORTED, PCCP_ERR_SCRATCH,
+                   PCCP_FIXPOINT,
                    PCCP_FAILED, PCCP_ERROR, PCCP_INPUT_ORDER, PCCP_FIRST_FAIL, PCCP_OPTIMISE,
                    PCCP_COUNT_ALL, PCCP_RES_OPTIMAL, PCCP_RES_INFEASIBLE, PCCP_RES_LIMIT,
                    INT32_MAX, PccpError, check, load, library_path)
@@ -23,6 +24,7 @@ from . import rcpsp  # noqa: F401
 
 __all__ = ["Model", "pccp_model_create", "pccp_model_destroy", "pccp_model_get_info",
            "pccp_propagate", "pccp_propagate_ex", "pccp_solve", "pccp_solve_batch",
+           "pccp_solve_batch_noalloc",
            "pccp_error_string", "propagate", "propagate_host", "solve", "solve_batch",
            "PccpError", "load", "library_path"]
 
@@ -74,6 +76,12 @@ def pccp_solve_batch(handles, opts, results, stream):
     n = len(handles)
     arr = (ctypes.c_void_p * n)(*[h.value for h in handles])
     return load().pccp_solve_batch(arr, n, ctypes.byref(opts), results, stream)
+
+
+def pccp_solve_batch_noalloc(handles, opts, results, stream):
+    n = len(handles)
+    arr = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    return load().pccp_solve_batch_noalloc(arr, n, ctypes.byref(opts), results, stream)
 
 
 def pccp_error_string(code):
@@ -225,13 +233,16 @@ def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, determini
 
 
 def solve_batch(models, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
-                node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None):
+                node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None, noalloc=False):
+    """Solve many models in one launch.  noalloc=True uses the allocation-free
+    entry point (fixed device scratch; see include/pccp.h)."""
     o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, threads, blocks)
     n = len(models)
     ws = [np.zeros(m.n_vars, dtype=np.int32) for m in models]
     res = (_abi.pccp_result * n)()
     for i in range(n):
         res[i].witness = ws[i].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-    rc = pccp_solve_batch([m.handle for m in models], o, res, _stream_ptr(stream))
-    check(rc, "pccp_solve_batch")
+    call = pccp_solve_batch_noalloc if noalloc else pccp_solve_batch
+    rc = call([m.handle for m in models], o, res, _stream_ptr(stream))
+    check(rc, call.__name__)
     return [_result_dict(res[i], ws[i]) for i in range(n)]

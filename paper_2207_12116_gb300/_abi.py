@@ -19,6 +19,7 @@ PCCP_ERR_SMEM = -3
 PCCP_ERR_TIMEOUT = -4
 PCCP_ERR_CUDA = -5
 PCCP_ERR_UNSUPPORTED = -6
+PCCP_ERR_SCRATCH = -7
 
 PCCP_FIXPOINT, PCCP_FAILED, PCCP_ERROR = 0, 1, 2
 PCCP_INPUT_ORDER, PCCP_FIRST_FAIL = 0, 1
@@ -74,6 +75,8 @@ SIGNATURES = {
     "pccp_solve": (ctypes.c_int, [P, ctypes.POINTER(pccp_solve_opts), ctypes.POINTER(pccp_result), P]),
     "pccp_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), I32, ctypes.POINTER(pccp_solve_opts),
                                         ctypes.POINTER(pccp_result), P]),
+    "pccp_solve_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(P), I32, ctypes.POINTER(pccp_solve_opts),
+                                                ctypes.POINTER(pccp_result), P]),
     "pccp_error_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
 

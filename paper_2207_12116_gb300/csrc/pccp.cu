@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cstdint>
 #include <cstdlib>
@@ -136,6 +137,9 @@ struct InstanceResult {
   int64_t nodes, fails, solutions, iterations;
   int32_t error, pad;
 };
+
+static_assert(sizeof(InstanceDesc) == 40, "descriptor size is part of the scratch accounting");
+static_assert(sizeof(InstanceResult) == 56, "result size is part of the scratch accounting");
 
 struct SolveArgs {
   const InstanceDesc* inst;
@@ -584,6 +588,7 @@ const char* pccp_error_string(int code) {
     case PCCP_ERR_TIMEOUT: return "a device wait or iteration budget ran out";
     case PCCP_ERR_CUDA: return "CUDA runtime error";
     case PCCP_ERR_UNSUPPORTED: return "model outside the packed-table limits";
+    case PCCP_ERR_SCRATCH: return "request exceeds the fixed scratch of the allocation-free call";
     default: return "unknown error";
   }
 }
@@ -854,3 +859,5 @@ int pccp_solve(const pccp_model* m, const pccp_solve_opts* opts, pccp_result* re
 }
 
 }  // extern "C"
+
+#include "pccp_noalloc.inc"
