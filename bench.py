@@ -45,10 +45,29 @@ def workload_config(n_vars, rows, extra=None):
     return cfg
 
 
-def build_inputs():
+def build_inputs(rank=0):
+    """The model and this rank's 10,000 nodes.  Ranks are independent
+    replicas: rank r draws its nodes with seed NODE_SEED + r (rank 0 is the
+    single-GPU workload)."""
     inst = config_instance(FAMILY, INSTANCE)
-    nodes = draw_partial_assignments(inst.n, inst.horizon, N_NODES, seed=NODE_SEED)
+    nodes = draw_partial_assignments(inst.n, inst.horizon, N_NODES, seed=NODE_SEED + rank)
     return inst, nodes
+
+
+def max_over_ranks(x, world, device):
+    """Largest value of x over all ranks (the slowest rank sets the time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms_max):
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1000.0)
 
 
 # ------------------------------------------------------------ CPU oracle leg
@@ -207,6 +226,91 @@ def launch_desc(args):
             "ctas_per_sm": args.ctas_per_sm, "linear_mode": args.linear_mode}
 
 
+KERNEL_SOURCES = ("paper_2207_12116_gb300/csrc/k_propagate.cuh",
+                  "paper_2207_12116_gb300/csrc/pccp_device.cuh")
+PROFILE = "profiles/k_propagate_j30_batch.md"
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of k_propagate from the committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    try:
+        text = open(os.path.join(ROOT, PROFILE)).read()
+    except OSError:
+        return None, None
+    rec = {}
+    for line in text.splitlines():
+        if line.startswith("<!-- ") and ":" in line:
+            k, v = line[5:].rstrip(" ->").split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("kernel_sha") != kernel_hash():
+        return None, "kernel changed since the committed ncu capture"
+    try:
+        return int(rec["dram_bytes_per_launch"]), PROFILE
+    except (KeyError, ValueError):
+        return None, None
+
+
+SEARCH_MODELS = 256
+SEARCH_NODE_LIMIT = 4000
+EPS_TIME_MS = 2000
+
+
+def search_bench(pccp, cpu=True):
+    """Search throughput: (a) one persistent launch solving 256 seeded
+    30-60-task models depth first, one team per model, each stopped after
+    4,000 nodes; (b) every team of the GPU on one 30-task model (subproblems
+    from breadth-first growth, shared incumbent) for 2 s; (c) the oracle on a
+    bounded sample of (a)."""
+    from synthetic import config_instance
+    insts = [config_instance("mixed30_60", s) for s in range(SEARCH_MODELS)]
+    models = [pccp.Model.from_rcpsp(i) for i in insts]
+    pccp.solve_batch(models[:8], node_limit=50)  # warm-up
+    res = pccp.solve_batch(models, node_limit=SEARCH_NODE_LIMIT)
+    ms = res[0]["elapsed_ms"]
+    nodes = sum(r["nodes"] for r in res)
+    rows = sum(r["rows_evaluated"] for r in res)
+    out = {"batched": {
+        "workload": f"{SEARCH_MODELS} models, 30-60 tasks, 4 resources, depth-first "
+                    f"input-order search, {SEARCH_NODE_LIMIT} nodes each, one launch",
+        "nodes_per_s": nodes / (ms / 1000), "propagator_evals_per_s": rows / (ms / 1000),
+        "ms": ms, "nodes": nodes,
+        "solutions_found": sum(r["solutions"] for r in res),
+        "iterations_per_node": sum(r["iterations"] for r in res) / max(nodes, 1)}}
+    m = pccp.Model.from_rcpsp(config_instance("j30", 0))
+    r = pccp.solve(m, deterministic=False, time_limit_ms=EPS_TIME_MS)
+    out["parallel"] = {
+        "workload": f"one 30-task model (j30/0), all teams, {EPS_TIME_MS} ms limit",
+        "nodes_per_s": r["nodes"] / (r["elapsed_ms"] / 1000),
+        "propagator_evals_per_s": r["rows_evaluated"] / (r["elapsed_ms"] / 1000),
+        "ms": r["elapsed_ms"], "nodes": r["nodes"], "status": r["status"],
+        "best_makespan": r["objective"]}
+    if cpu:
+        import oracle
+        from oracle.rcpsp import rcpsp_model
+        from concurrent.futures import ThreadPoolExecutor
+        cores = os.cpu_count() or 1
+        sample = insts[:cores]
+        lim = 400
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(cores) as ex:
+            rs = list(ex.map(lambda i: oracle.solve(rcpsp_model(i), node_limit=lim), sample))
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"kind": "oracle", "cores": cores,
+                               "nodes_per_s": sum(x["nodes"] for x in rs) / dt,
+                               "sample": f"first {len(sample)} of the {SEARCH_MODELS} models, "
+                                         f"{lim} nodes each, one thread per model ({dt:.1f} s)"}
+    return out
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -227,7 +331,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    inst, nodes = build_inputs()
+    inst, nodes = build_inputs(rank)
     rows = pccp.rcpsp.build_rows(inst)
     model = pccp.Model.from_rows(rows)
     lb_h, ub_h = pccp.rcpsp.node_stores(rows, nodes)
@@ -275,10 +379,7 @@ def run_gpu(args):
     clk = clocks.stop()
     kernel_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(kernel_ms)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, world, dev)
 
     st = status.cpu().numpy()
     it = iters.cpu().numpy().astype(np.int64)
@@ -314,10 +415,7 @@ def run_gpu(args):
             b.synchronize()
             if k >= args.warmup:
                 e2e_ms.append(a.elapsed_time(b))
-        e2e_t = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-        e2e_v = world * N_NODES / (float(e2e_t.item()) / 1000)
+        e2e_v = whole_job_rate(world, N_NODES, max_over_ranks(statistics.mean(e2e_ms), world, dev))
         assert np.array_equal(out_st.numpy(), st), "end-to-end results differ from device-timed run"
         e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * nv * N_NODES,
                "d2h_bytes_per_step": 2 * 4 * nv * N_NODES + 4 * N_NODES}
@@ -330,8 +428,9 @@ def run_gpu(args):
         smem_peak = sms * 128 * (sm_mhz or 0) * 1e6 / 1e9  # GB/s: 128 B/clk/SM
         achieved = bytes_smem / (ms / 1000) / 1e9
         hbm_peak = peaks.get("hbm_gbs")
+        traffic, traffic_src = recorded_traffic()
         line = {
-            "metric": METRIC, "value": world * N_NODES / (ms_max / 1000), "unit": UNIT,
+            "metric": METRIC, "value": whole_job_rate(world, N_NODES, ms_max), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
@@ -342,7 +441,7 @@ def run_gpu(args):
             "failed_nodes": int((st == 1).sum()),
             "roofline": {"bound": "smem", "achieved": achieved, "peak": smem_peak,
                          "unit": "GB/s", "frac": achieved / smem_peak if smem_peak else None,
-                         "traffic": None,
+                         "traffic": traffic, "traffic_source": traffic_src,
                          "peak_source": f"derived: {sms} SMs x 128 B/clk x {sm_mhz} MHz "
                                         f"(median SM clock sampled during the run)",
                          "algorithmic_bytes_per_launch": bytes_smem,
@@ -358,6 +457,8 @@ def run_gpu(args):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(inst, nodes)
+        if not args.no_search:
+            line["search"] = search_bench(pccp, cpu=not args.no_cpu_baseline)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -372,6 +473,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-search", action="store_true")
     ap.add_argument("--team", type=int, default=0, help="threads per team (0: library default)")
     ap.add_argument("--teams", type=int, default=0, help="teams per CTA (0: library default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)

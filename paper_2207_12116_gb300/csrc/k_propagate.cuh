@@ -1,0 +1,93 @@
+// k_propagate.cuh -- the batched propagation kernel (included by pccp.cu).
+//
+// Persistent CTAs; the packed propagator table is brought into shared memory
+// once per CTA by TMA bulk copies; each team of warps pulls stores from a
+// global counter, stages one store (joined with the root domains) into
+// shared memory and runs the lock-free fixed-point loop on it (Sec. 4-5).
+#pragma once
+
+#include "pccp_device.cuh"
+
+namespace pccp {
+
+struct PropArgs {
+  const uint8_t* image;
+  const int2* root;
+  int32_t* lb;
+  int32_t* ub;
+  int32_t* status;
+  int32_t* iters;
+  int* counter;
+  uint32_t image_bytes;
+  int n_vars;
+  int n_stores;
+  int team_size;
+  int teams;
+  int max_iter;
+  int linear_mode;
+};
+
+// Instantiated for 1024-thread CTAs (one per SM) and for CTAs of up to 512
+// threads with three resident per SM (registers capped for 48 warps/SM).
+template <int kMaxThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* img = smem;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + a.image_bytes);
+  int* ctrl_base = reinterpret_cast<int*>(smem + a.image_bytes + 16);
+  int2* st_base = reinterpret_cast<int2*>(smem + a.image_bytes + 16 + 16 * a.teams);
+
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  const bool ok = load_image(img, a.image, a.image_bytes, mbar, 0);
+
+  const int team_id = threadIdx.x / a.team_size;
+  Team tm;
+  tm.tid = threadIdx.x - team_id * a.team_size;
+  tm.nthr = a.team_size;
+  tm.bar = 1 + team_id;
+  tm.lane = threadIdx.x & 31;
+  tm.warp = tm.tid >> 5;
+  tm.nwarps = a.team_size >> 5;
+  int* ctrl = ctrl_base + 4 * team_id;  // [0] next store, [1] failure flag
+  int2* st = st_base + static_cast<size_t>(team_id) * a.n_vars;
+  const Tab tb = make_tab(img);
+  const int nv = a.n_vars;
+
+  for (;;) {
+    if (tm.tid == 0) ctrl[0] = atomicAdd(a.counter, 1);
+    team_bar(tm.bar, tm.nthr);
+    const int s = ctrl[0];
+    if (s >= a.n_stores) break;
+    if (!ok) {  // table never arrived: report the stores this team takes
+      if (tm.tid == 0) {
+        a.status[s] = kError;
+        if (a.iters) a.iters[s] = 0;
+      }
+      continue;
+    }
+    int32_t* lbs = a.lb + static_cast<size_t>(s) * nv;
+    int32_t* ubs = a.ub + static_cast<size_t>(s) * nv;
+    bool empty = false;
+    for (int v = tm.tid; v < nv; v += tm.nthr) {
+      const int2 r = __ldg(a.root + v);
+      const int l = max(lbs[v], r.x), u = min(ubs[v], r.y);
+      st[v] = make_int2(l, u);
+      empty |= l > u;
+    }
+    if (tm.tid == 0) ctrl[1] = 0;
+    const bool any_empty = team_bar_or(tm.bar, tm.nthr, empty);
+    int status = kFailed, it = 0;
+    if (!any_empty) status = team_fixpoint(tb, st, tm, &ctrl[1], a.max_iter, it, a.linear_mode);
+    for (int v = tm.tid; v < nv; v += tm.nthr) {
+      const int2 D = st[v];
+      lbs[v] = D.x;
+      ubs[v] = D.y;
+    }
+    if (tm.tid == 0) {
+      a.status[s] = status;
+      if (a.iters) a.iters[s] = it;
+    }
+  }
+}
+
+}  // namespace pccp

@@ -1,0 +1,420 @@
+// k_solve_eps.cuh -- parallel search of one model by every team of the GPU
+// (included by pccp.cu).
+//
+// Embarrassingly parallel search (the EPS variant of Sec. 5): the tree is
+// first grown breadth first, one level per launch of k_eps_expand, until the
+// frontier holds enough subproblems for every team; each subproblem is a
+// decision path.  k_eps_solve then runs persistent teams that pull paths from
+// a global counter and search each subtree depth first with full
+// recomputation from the root store (Sec. 5).  The teams share the incumbent
+// through a global atomicMin: every node is told ub(obj) <= best - 1 with the
+// best objective known when the node starts (branch and bound).
+#pragma once
+
+#include "pccp_device.cuh"
+
+namespace pccp {
+
+// Search state shared by every team of both kernels (global memory).
+struct EpsGlobal {
+  int best;      // incumbent objective, INT_MAX while none
+  int stop;      // 1: stop at the next node (limit reached, or satisfied)
+  int limited;   // a node or time limit stopped the search
+  int error;     // 1 iteration budget, 2 decision stack, 3 table load, 4 frontier overflow
+  unsigned long long t0;          // globaltimer at the first node (0 until set)
+  unsigned long long live_nodes;  // node count published in batches, for the limit
+  unsigned long long nodes, fails, solutions, iterations;
+  int max_depth;
+  int pad[3];
+};
+
+struct EpsArgs {
+  const uint8_t* image;
+  const int2* root;
+  EpsGlobal* g;
+  int* team_best;        // [n_teams]: objective of the team's recorded witness
+  int* team_has;         // [n_teams]: 1 if the team recorded a witness
+  int32_t* witness;      // [n_teams][n_vars]
+  int2* stacks;          // [n_teams][max_depth]
+  const int2* in_paths;  // [n_in][in_len]
+  int2* out_paths;       // [out_cap][in_len + 1] (expansion only)
+  int* in_counter;
+  int* out_count;
+  uint32_t image_bytes;
+  int n_vars;
+  int max_iter;
+  int teams;             // per CTA
+  int team_size;
+  int n_in;
+  int in_len;
+  int out_cap;
+  int max_depth;
+  int mode;
+  int strategy;
+  int obj_ub;
+  int linear_mode;
+  int64_t node_limit;
+  int64_t time_limit_ns;
+};
+
+struct EpsCtrl {
+  unsigned long long sel[2];
+  int fail;
+  int stop;
+  int record;
+  int err;
+  int depth;
+  int next;
+  int out;
+  int pad[5];
+};
+
+enum : int { kNodeFailed = 0, kNodeSolution = 1, kNodeBranch = 2, kNodeStop = 3, kNodeError = 4 };
+
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t eps_now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// One node: limits and incumbent bound (thread 0), fixed point, selection.
+// The caller has put root join decisions into st; the first barrier here
+// orders those writes before the fixed point.  On kNodeBranch, *key holds
+// the selection key (branch index in the low 32 bits).  Team-uniform result.
+// Broadcast slots follow the protocol of team_dfs: written before a barrier,
+// read after it, not rewritten before another barrier has passed.
+__device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm, EpsCtrl* sc,
+                                        unsigned par, const EpsArgs& a, int& it,
+                                        unsigned long long& key) {
+  EpsGlobal* g = a.g;
+  if (tm.tid == 0) {
+    int stop = ld_relaxed_gpu(&g->stop);
+    if (!stop && a.time_limit_ns > 0) {
+      const unsigned long long t0 = *reinterpret_cast<volatile unsigned long long*>(&g->t0);
+      if (t0 != 0 && static_cast<int64_t>(eps_now_ns() - t0) > a.time_limit_ns) {
+        atomicExch(&g->limited, 1);
+        atomicExch(&g->stop, 1);
+        stop = 1;
+      }
+    }
+    if (!stop && tb.objective >= 0) {
+      int bound = a.obj_ub;
+      if (a.mode == PCCP_OPTIMISE) {
+        const int gb = ld_relaxed_gpu(&g->best);
+        if (gb != INT_MAX) bound = min(bound, gb - 1);
+      }
+      if (bound < INT_MAX) atom_min_s32(&st[tb.objective].y, bound);
+    }
+    sc->stop = stop;
+    sc->fail = 0;
+    sc->sel[par] = ~0ull;
+  }
+  team_bar(tm.bar, tm.nthr);
+  if (sc->stop) return kNodeStop;
+  const int fst = team_fixpoint(tb, st, tm, &sc->fail, a.max_iter, it, a.linear_mode);
+  if (fst == kError) return kNodeError;
+  if (fst == kFailed) return kNodeFailed;
+  unsigned long long* sel = &sc->sel[par];
+  for (int k = tm.tid; k < tb.n_branch; k += tm.nthr) {
+    const int v = tb.branch[k];
+    const int2 D = ld_dom(st, v);
+    if (D.x < D.y) {
+      unsigned long long kk = static_cast<unsigned long long>(k);
+      if (a.strategy == PCCP_FIRST_FAIL)
+        kk |= static_cast<unsigned long long>(static_cast<uint32_t>(D.y - D.x)) << 32;
+      atomicMin(sel, kk);
+      if (a.strategy == PCCP_INPUT_ORDER) break;
+    }
+  }
+  team_bar(tm.bar, tm.nthr);
+  key = *sel;
+  return key == ~0ull ? kNodeSolution : kNodeBranch;
+}
+
+// A solution was found on st: publish it to the incumbent, record the
+// team's witness when it improves (optimise) or is the team's first
+// (count-all), stop everything when there is no objective.  Ends with a
+// barrier; team-uniform.
+__device__ __forceinline__ void eps_solution(const Tab& tb, int2* st, const Team& tm, EpsCtrl* sc,
+                                             const EpsArgs& a, int team_gid,
+                                             unsigned long long& sols) {
+  EpsGlobal* g = a.g;
+  if (tm.tid == 0) {
+    ++sols;
+    const int z = tb.objective >= 0 ? st[tb.objective].x : 0;
+    bool record;
+    if (a.mode == PCCP_OPTIMISE && tb.objective >= 0) {
+      const int old = atomicMin(&g->best, z);
+      record = z < old;
+    } else {
+      record = a.team_has[team_gid] == 0;
+      if (tb.objective >= 0) atomicMin(&g->best, z);
+    }
+    if (a.mode == PCCP_OPTIMISE && tb.objective < 0) atomicExch(&g->stop, 1);
+    if (record) {
+      a.team_best[team_gid] = z;
+      a.team_has[team_gid] = 1;
+    }
+    sc->record = record;
+  }
+  team_bar(tm.bar, tm.nthr);
+  if (sc->record) {
+    int32_t* w = a.witness + static_cast<size_t>(team_gid) * a.n_vars;
+    for (int v = tm.tid; v < a.n_vars; v += tm.nthr) w[v] = st[v].x;
+  }
+}
+
+__device__ __forceinline__ void eps_restore(const int2* root, int2* st, const Team& tm, int nv,
+                                            const int2* path, int len) {
+  for (int v = tm.tid; v < nv; v += tm.nthr) st[v] = __ldg(root + v);
+  team_bar(tm.bar, tm.nthr);
+  for (int k = tm.tid; k < len; k += tm.nthr) {
+    const int2 e = path[k];
+    const int v = static_cast<int>(static_cast<uint32_t>(e.x) & 0x7fffffffu);
+    if (static_cast<uint32_t>(e.x) & 0x80000000u)
+      atom_max_s32(&st[v].x, e.y);
+    else
+      atom_min_s32(&st[v].y, e.y);
+  }
+}
+
+__device__ __forceinline__ void eps_count_node(const EpsArgs& a, unsigned long long& local,
+                                               unsigned long long& published) {
+  ++local;
+  if (a.node_limit > 0 && local - published >= 64) {
+    const unsigned long long n = atomicAdd(&a.g->live_nodes, local - published) + (local - published);
+    published = local;
+    if (n >= static_cast<unsigned long long>(a.node_limit)) {
+      atomicExch(&a.g->limited, 1);
+      atomicExch(&a.g->stop, 1);
+    }
+  }
+}
+
+struct EpsSmem {
+  uint8_t* img;
+  uint64_t* mbar;
+  EpsCtrl* sc;
+  int2* st;
+};
+
+__device__ __forceinline__ EpsSmem eps_smem(uint8_t* smem, const EpsArgs& a, int team_id) {
+  EpsSmem s;
+  s.img = smem;
+  s.mbar = reinterpret_cast<uint64_t*>(smem + a.image_bytes);
+  EpsCtrl* ctrl = reinterpret_cast<EpsCtrl*>(smem + a.image_bytes + 16);
+  s.sc = ctrl + team_id;
+  int2* st_base = reinterpret_cast<int2*>(smem + a.image_bytes + 16 + sizeof(EpsCtrl) * a.teams);
+  s.st = st_base + static_cast<size_t>(team_id) * a.n_vars;
+  return s;
+}
+
+__device__ __forceinline__ Team eps_team(const EpsArgs& a, int team_id) {
+  Team tm;
+  tm.tid = threadIdx.x - team_id * a.team_size;
+  tm.nthr = a.team_size;
+  tm.bar = 1 + team_id;
+  tm.lane = threadIdx.x & 31;
+  tm.warp = tm.tid >> 5;
+  tm.nwarps = a.team_size >> 5;
+  return tm;
+}
+
+// One breadth-first level: every input path is propagated once; failures
+// and solutions are counted; every other node pushes its two children
+// (left ub <= m, right lb >= m + 1) to the output level.
+__global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int team_id = threadIdx.x / a.team_size;
+  const EpsSmem sm = eps_smem(smem, a, team_id);
+  if (threadIdx.x == 0) mbar_init(sm.mbar, 1);
+  if (!load_image(sm.img, a.image, a.image_bytes, sm.mbar, 0)) {
+    if (threadIdx.x == 0) atomicExch(&a.g->error, 3);
+    return;
+  }
+  if (threadIdx.x == 0 && blockIdx.x == 0 && a.g->t0 == 0)
+    atomicCAS(&a.g->t0, 0ull, static_cast<unsigned long long>(eps_now_ns()));
+  const Team tm = eps_team(a, team_id);
+  const Tab tb = make_tab(sm.img);
+  const int team_gid = blockIdx.x * a.teams + team_id;
+  EpsCtrl* sc = sm.sc;
+  unsigned long long nodes = 0, published = 0, fails = 0, sols = 0, iters = 0;
+  int max_d = 0;
+  unsigned par = 0;
+  for (;;) {
+    if (tm.tid == 0) sc->next = atomicAdd(a.in_counter, 1);
+    team_bar(tm.bar, tm.nthr);
+    const int p = sc->next;
+    if (p >= a.n_in) break;
+    const int2* path = a.in_paths + static_cast<size_t>(p) * a.in_len;
+    eps_restore(a.root, sm.st, tm, a.n_vars, path, a.in_len);
+    int it = 0;
+    unsigned long long key = 0;
+    const int r = eps_node(tb, sm.st, tm, sc, par, a, it, key);
+    par ^= 1u;
+    if (r == kNodeStop) break;
+    if (tm.tid == 0) {
+      eps_count_node(a, nodes, published);
+      iters += it;
+      max_d = max(max_d, a.in_len);
+    }
+    if (r == kNodeError) {
+      if (tm.tid == 0) atomicExch(&a.g->error, 1);
+      break;
+    }
+    if (r == kNodeFailed) {
+      if (tm.tid == 0) ++fails;
+      continue;
+    }
+    if (r == kNodeSolution) {
+      eps_solution(tb, sm.st, tm, sc, a, team_gid, sols);
+      continue;
+    }
+    // branch: two children appended to the next level
+    if (tm.tid == 0) {
+      const int o = atomicAdd(a.out_count, 2);
+      if (o + 2 > a.out_cap) {
+        atomicExch(&a.g->error, 4);
+        sc->out = -1;
+      } else {
+        const int v = tb.branch[static_cast<int>(key & 0xffffffffull)];
+        const int2 D = sm.st[v];
+        const int m = D.x + (D.y - D.x) / 2;
+        const size_t w = static_cast<size_t>(a.in_len) + 1;
+        a.out_paths[static_cast<size_t>(o) * w + a.in_len] = make_int2(v, m);
+        a.out_paths[static_cast<size_t>(o + 1) * w + a.in_len] =
+            make_int2(static_cast<int>(static_cast<uint32_t>(v) | 0x80000000u), m + 1);
+        sc->out = o;
+      }
+    }
+    team_bar(tm.bar, tm.nthr);
+    const int o = sc->out;
+    if (o < 0) break;
+    const size_t w = static_cast<size_t>(a.in_len) + 1;
+    for (int k = tm.tid; k < a.in_len; k += tm.nthr) {
+      const int2 e = path[k];
+      a.out_paths[static_cast<size_t>(o) * w + k] = e;
+      a.out_paths[static_cast<size_t>(o + 1) * w + k] = e;
+    }
+  }
+  if (tm.tid == 0) {
+    atomicAdd(&a.g->nodes, nodes);
+    atomicAdd(&a.g->fails, fails);
+    atomicAdd(&a.g->solutions, sols);
+    atomicAdd(&a.g->iterations, iters);
+    atomicMax(&a.g->max_depth, max_d);
+  }
+}
+
+// Persistent teams search the subtrees under the frontier paths depth first.
+__global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int team_id = threadIdx.x / a.team_size;
+  const EpsSmem sm = eps_smem(smem, a, team_id);
+  if (threadIdx.x == 0) mbar_init(sm.mbar, 1);
+  if (!load_image(sm.img, a.image, a.image_bytes, sm.mbar, 0)) {
+    if (threadIdx.x == 0) atomicExch(&a.g->error, 3);
+    return;
+  }
+  if (threadIdx.x == 0 && blockIdx.x == 0 && a.g->t0 == 0)
+    atomicCAS(&a.g->t0, 0ull, static_cast<unsigned long long>(eps_now_ns()));
+  const Team tm = eps_team(a, team_id);
+  const Tab tb = make_tab(sm.img);
+  const int team_gid = blockIdx.x * a.teams + team_id;
+  EpsCtrl* sc = sm.sc;
+  int2* stack = a.stacks + static_cast<size_t>(team_gid) * a.max_depth;
+  const int base = a.in_len;
+  unsigned long long nodes = 0, published = 0, fails = 0, sols = 0, iters = 0;
+  int max_d = 0;
+  unsigned par = 0;
+  bool done = false;
+  while (!done) {
+    if (tm.tid == 0) sc->next = atomicAdd(a.in_counter, 1);
+    team_bar(tm.bar, tm.nthr);
+    const int p = sc->next;
+    if (p >= a.n_in) break;
+    const int2* path = a.in_paths + static_cast<size_t>(p) * base;
+    for (int k = tm.tid; k < base; k += tm.nthr) stack[k] = path[k];
+    int depth = base;  // thread 0's copy is authoritative
+    eps_restore(a.root, sm.st, tm, a.n_vars, path, base);
+    for (;;) {
+      int it = 0;
+      unsigned long long key = 0;
+      const int r = eps_node(tb, sm.st, tm, sc, par, a, it, key);
+      par ^= 1u;
+      if (r == kNodeStop) {
+        done = true;
+        break;
+      }
+      if (tm.tid == 0) {
+        eps_count_node(a, nodes, published);
+        iters += it;
+        max_d = max(max_d, depth);
+      }
+      if (r == kNodeError) {
+        if (tm.tid == 0) atomicExch(&a.g->error, 1);
+        done = true;
+        break;
+      }
+      if (r == kNodeBranch) {
+        if (tm.tid == 0) {
+          int err = 0;
+          if (depth >= a.max_depth) {
+            err = 1;
+            atomicExch(&a.g->error, 2);
+          } else {
+            const int v = tb.branch[static_cast<int>(key & 0xffffffffull)];
+            const int2 D = sm.st[v];
+            const int m = D.x + (D.y - D.x) / 2;
+            stack[depth] = make_int2(v, m);
+            ++depth;
+            atom_min_s32(&sm.st[v].y, m);
+          }
+          sc->err = err;
+        }
+        team_bar(tm.bar, tm.nthr);
+        if (sc->err) {
+          done = true;
+          break;
+        }
+        continue;
+      }
+      if (r == kNodeFailed) {
+        if (tm.tid == 0) ++fails;
+      } else {
+        eps_solution(tb, sm.st, tm, sc, a, team_gid, sols);
+      }
+      // backtrack within the subtree: never above the subproblem's path
+      if (tm.tid == 0) {
+        while (depth > base && (static_cast<uint32_t>(stack[depth - 1].x) & 0x80000000u)) --depth;
+        if (depth == base) {
+          sc->depth = -1;
+        } else {
+          const int2 e = stack[depth - 1];
+          stack[depth - 1] =
+              make_int2(static_cast<int>(static_cast<uint32_t>(e.x) | 0x80000000u), e.y + 1);
+          sc->depth = depth;
+        }
+      }
+      team_bar(tm.bar, tm.nthr);
+      const int d = sc->depth;
+      if (d < 0) break;  // subtree exhausted: next subproblem
+      eps_restore(a.root, sm.st, tm, a.n_vars, stack, d);
+    }
+  }
+  if (tm.tid == 0) {
+    atomicAdd(&a.g->nodes, nodes);
+    atomicAdd(&a.g->fails, fails);
+    atomicAdd(&a.g->solutions, sols);
+    atomicAdd(&a.g->iterations, iters);
+    atomicMax(&a.g->max_depth, max_d);
+  }
+}
+
+}  // namespace pccp

@@ -24,6 +24,8 @@
 
 #include "../../include/pccp.h"
 #include "pccp_device.cuh"
+#include "k_propagate.cuh"
+#include "k_solve_eps.cuh"
 
 using namespace pccp;
 
@@ -38,85 +40,6 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-// ------------------------------------------------------------- propagation
-
-struct PropArgs {
-  const uint8_t* image;
-  const int2* root;
-  int32_t* lb;
-  int32_t* ub;
-  int32_t* status;
-  int32_t* iters;
-  int* counter;
-  uint32_t image_bytes;
-  int n_vars;
-  int n_stores;
-  int team_size;
-  int teams;
-  int max_iter;
-  int linear_mode;
-};
-
-__global__ void __launch_bounds__(1024) k_propagate(PropArgs a) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t* img = smem;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + a.image_bytes);
-  int* ctrl_base = reinterpret_cast<int*>(smem + a.image_bytes + 16);
-  int2* st_base = reinterpret_cast<int2*>(smem + a.image_bytes + 16 + 16 * a.teams);
-
-  if (threadIdx.x == 0) mbar_init(mbar, 1);
-  const bool ok = load_image(img, a.image, a.image_bytes, mbar, 0);
-
-  const int team_id = threadIdx.x / a.team_size;
-  Team tm;
-  tm.tid = threadIdx.x - team_id * a.team_size;
-  tm.nthr = a.team_size;
-  tm.bar = 1 + team_id;
-  tm.lane = threadIdx.x & 31;
-  tm.warp = tm.tid >> 5;
-  tm.nwarps = a.team_size >> 5;
-  int* ctrl = ctrl_base + 4 * team_id;  // [0] next store, [1] failure flag
-  int2* st = st_base + static_cast<size_t>(team_id) * a.n_vars;
-  const Tab tb = make_tab(img);
-  const int nv = a.n_vars;
-
-  for (;;) {
-    if (tm.tid == 0) ctrl[0] = atomicAdd(a.counter, 1);
-    team_bar(tm.bar, tm.nthr);
-    const int s = ctrl[0];
-    if (s >= a.n_stores) break;
-    if (!ok) {  // table never arrived: report the stores this team takes
-      if (tm.tid == 0) {
-        a.status[s] = kError;
-        if (a.iters) a.iters[s] = 0;
-      }
-      continue;
-    }
-    int32_t* lbs = a.lb + static_cast<size_t>(s) * nv;
-    int32_t* ubs = a.ub + static_cast<size_t>(s) * nv;
-    bool empty = false;
-    for (int v = tm.tid; v < nv; v += tm.nthr) {
-      const int2 r = __ldg(a.root + v);
-      const int l = max(lbs[v], r.x), u = min(ubs[v], r.y);
-      st[v] = make_int2(l, u);
-      empty |= l > u;
-    }
-    if (tm.tid == 0) ctrl[1] = 0;
-    const bool any_empty = team_bar_or(tm.bar, tm.nthr, empty);
-    int status = kFailed, it = 0;
-    if (!any_empty) status = team_fixpoint(tb, st, tm, &ctrl[1], a.max_iter, it, a.linear_mode);
-    for (int v = tm.tid; v < nv; v += tm.nthr) {
-      const int2 D = st[v];
-      lbs[v] = D.x;
-      ubs[v] = D.y;
-    }
-    if (tm.tid == 0) {
-      a.status[s] = status;
-      if (a.iters) a.iters[s] = it;
-    }
-  }
 }
 
 // ------------------------------------------------------------------ search
@@ -433,6 +356,11 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
                                 (static_cast<uint32_t>(static_cast<uint16_t>(dd)) << 16)));
     bytes_per_sweep += 40;
   }
+  // Reified rows sorted by their Boolean: rows evaluated side by side by one
+  // warp then touch neighbouring variables (fewer shared-memory bank
+  // conflicts).  Row order never changes the fixed point (Sec. 3).
+  std::stable_sort(RF.begin(), RF.end(),
+                   [](const uint2& p, const uint2& q) { return (p.y & 0xffffu) < (q.y & 0xffffu); });
   if (d->n_linear > 0 && d->linear_off[0] != 0) return PCCP_ERR_INVALID;
   for (int32_t i = 0; i < d->n_linear; ++i) {
     const int32_t o0 = d->linear_off[i], o1 = d->linear_off[i + 1];
@@ -532,6 +460,7 @@ int check_device(const pccp_model* m) {
   } while (0)
 
 struct PropPlan {
+  void (*kern)(PropArgs);
   int team, teams, grid;
   size_t smem;
 };
@@ -554,13 +483,14 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   if (cfg && cfg->teams_per_cta > 0 && teams < cfg->teams_per_cta) return PCCP_ERR_SMEM;
   if (teams < 1) return PCCP_ERR_SMEM;
   const size_t smem = base + static_cast<size_t>(teams) * per_team;
-  if (cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const auto kern = (teams * team <= 512) ? k_propagate<512, 3> : k_propagate<1024, 1>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess) {
     (void)cudaGetLastError();
     return PCCP_ERR_CUDA;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate, teams * team, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, teams * team, smem) !=
       cudaSuccess) {
     (void)cudaGetLastError();
     return PCCP_ERR_CUDA;
@@ -568,6 +498,7 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   if (per_sm < 1) return PCCP_ERR_SMEM;
   if (cfg && cfg->ctas_per_sm > 0) per_sm = std::min(per_sm, static_cast<int>(cfg->ctas_per_sm));
   const int want = (n_stores + teams - 1) / teams;
+  p->kern = kern;
   p->team = team;
   p->teams = teams;
   p->grid = std::max(1, std::min(want, sms * per_sm));
@@ -697,7 +628,7 @@ int pccp_propagate_ex(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_
   a.teams = plan.teams;
   a.max_iter = (cfg && cfg->max_iterations > 0) ? cfg->max_iterations : m->max_iter;
   a.linear_mode = (cfg && cfg->linear_mode > 0) ? cfg->linear_mode - 1 : kDefaultLinearMode;
-  k_propagate<<<plan.grid, plan.team * plan.teams, plan.smem, s>>>(a);
+  plan.kern<<<plan.grid, plan.team * plan.teams, plan.smem, s>>>(a);
   const cudaError_t le = cudaGetLastError();
   cudaFreeAsync(counter, s);
   if (le != cudaSuccess) return PCCP_ERR_CUDA;
@@ -848,10 +779,213 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
   return rc;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Parallel search of one model: breadth-first frontier growth, then one
+// persistent launch over the frontier's subproblems (k_solve_eps.cuh).
+int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* res,
+                   cudaStream_t s) {
+  const int smem_max = max_dyn_smem();
+  const int sms = sm_count();
+  if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
+  const int team = o->threads > 0 ? o->threads : 128;
+  if (team % 32 != 0 || team > 1024) return PCCP_ERR_INVALID;
+  const size_t base = static_cast<size_t>(m->image_bytes) + 16;
+  const size_t per_team = sizeof(EpsCtrl) + static_cast<size_t>(m->n_vars) * sizeof(int2);
+  if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
+  const int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
+  const int teams = std::max(1, std::min({8, fit, 1024 / team}));
+  const size_t smem = base + static_cast<size_t>(teams) * per_team;
+  PCCP_CUDA(cudaFuncSetAttribute(k_eps_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem)));
+  PCCP_CUDA(cudaFuncSetAttribute(k_eps_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem)));
+  int occ_e = 0, occ_s = 0;
+  PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_e, k_eps_expand, teams * team, smem));
+  PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_eps_solve, teams * team, smem));
+  const int per_sm = std::min(occ_e, occ_s);
+  if (per_sm < 1) return PCCP_ERR_SMEM;
+  int grid = sms * per_sm;
+  if (o->blocks > 0) grid = std::min(grid, static_cast<int>(o->blocks));
+  const int n_teams = grid * teams;
+  const int max_depth = 32 * std::max(m->n_branch, 1) + 2;
+  const int target = 4 * n_teams;
+  constexpr int kMaxSeedLen = 48;
+  const size_t cap = 2 * static_cast<size_t>(target);
+  const size_t level_bytes = cap * (kMaxSeedLen + 1) * sizeof(int2);
+
+  const size_t o_g = 0;
+  const size_t o_tb = align16(o_g + sizeof(EpsGlobal));
+  const size_t o_th = align16(o_tb + static_cast<size_t>(n_teams) * sizeof(int));
+  const size_t o_w = align16(o_th + static_cast<size_t>(n_teams) * sizeof(int));
+  const size_t o_stk = align16(o_w + static_cast<size_t>(n_teams) * m->n_vars * sizeof(int32_t));
+  const size_t o_la = align16(o_stk + static_cast<size_t>(n_teams) * max_depth * sizeof(int2));
+  const size_t o_lb = align16(o_la + level_bytes);
+  const size_t o_cnt = align16(o_lb + level_bytes);
+  const size_t total = o_cnt + 16;
+  uint8_t* d = nullptr;
+  PCCP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), total, s));
+  int rc = PCCP_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  EpsGlobal hg;
+  std::vector<int> tbest(n_teams), thas(n_teams);
+  int n_final = 0, final_len = 0;
+  uint8_t* final_paths = nullptr;
+  do {
+    std::memset(&hg, 0, sizeof(hg));
+    hg.best = INT_MAX;
+    if (cudaMemsetAsync(d, 0, o_la, s) != cudaSuccess ||
+        cudaMemcpyAsync(d + o_g, &hg, sizeof(hg), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      rc = PCCP_ERR_CUDA;
+      break;
+    }
+    EpsArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.image = m->d_mem;
+    a.root = m->d_root;
+    a.g = reinterpret_cast<EpsGlobal*>(d + o_g);
+    a.team_best = reinterpret_cast<int*>(d + o_tb);
+    a.team_has = reinterpret_cast<int*>(d + o_th);
+    a.witness = reinterpret_cast<int32_t*>(d + o_w);
+    a.stacks = reinterpret_cast<int2*>(d + o_stk);
+    a.in_counter = reinterpret_cast<int*>(d + o_cnt);
+    a.out_count = reinterpret_cast<int*>(d + o_cnt + 4);
+    a.image_bytes = m->image_bytes;
+    a.n_vars = m->n_vars;
+    a.max_iter = m->max_iter;
+    a.teams = teams;
+    a.team_size = team;
+    a.max_depth = max_depth;
+    a.mode = o->mode;
+    a.strategy = o->strategy;
+    a.obj_ub = o->obj_ub;
+    a.linear_mode = kDefaultLinearMode;
+    a.node_limit = o->node_limit;
+    a.time_limit_ns = o->time_limit_ms > 0 ? o->time_limit_ms * 1000000ll : 0;
+    uint8_t* lin = d + o_la;
+    uint8_t* lout = d + o_lb;
+    int n_in = 1, len = 0;
+    bool finished = false;
+    cudaEventRecord(e0, s);
+    // breadth-first growth of the frontier
+    while (n_in < target && len < kMaxSeedLen) {
+      a.in_paths = reinterpret_cast<const int2*>(lin);
+      a.out_paths = reinterpret_cast<int2*>(lout);
+      a.n_in = n_in;
+      a.in_len = len;
+      a.out_cap = static_cast<int>(cap);
+      if (cudaMemsetAsync(d + o_cnt, 0, 16, s) != cudaSuccess) {
+        rc = PCCP_ERR_CUDA;
+        break;
+      }
+      k_eps_expand<<<grid, teams * team, smem, s>>>(a);
+      if (cudaGetLastError() != cudaSuccess) {
+        rc = PCCP_ERR_CUDA;
+        break;
+      }
+      int n_out = 0;
+      if (cudaMemcpyAsync(&n_out, a.out_count, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(&hg, d + o_g, sizeof(hg), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = PCCP_ERR_CUDA;
+        break;
+      }
+      if (hg.error || hg.stop || n_out == 0) {
+        finished = true;  // error, limit, satisfied, or the tree ended while growing
+        break;
+      }
+      std::swap(lin, lout);
+      n_in = n_out;
+      ++len;
+    }
+    if (rc != PCCP_OK) break;
+    if (!finished) {
+      n_final = n_in;
+      final_len = len;
+      final_paths = lin;
+      a.in_paths = reinterpret_cast<const int2*>(final_paths);
+      a.out_paths = nullptr;
+      a.n_in = n_final;
+      a.in_len = final_len;
+      a.out_cap = 0;
+      if (cudaMemsetAsync(d + o_cnt, 0, 16, s) != cudaSuccess) {
+        rc = PCCP_ERR_CUDA;
+        break;
+      }
+      k_eps_solve<<<grid, teams * team, smem, s>>>(a);
+      if (cudaGetLastError() != cudaSuccess) {
+        rc = PCCP_ERR_CUDA;
+        break;
+      }
+    }
+    cudaEventRecord(e1, s);
+    if (cudaMemcpyAsync(&hg, d + o_g, sizeof(hg), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(tbest.data(), d + o_tb, n_teams * sizeof(int), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(thas.data(), d + o_th, n_teams * sizeof(int), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = PCCP_ERR_CUDA;
+      break;
+    }
+    int winner = -1;
+    for (int t = 0; t < n_teams; ++t) {
+      if (!thas[t]) continue;
+      if (o->mode == PCCP_OPTIMISE && m->objective >= 0 && tbest[t] != hg.best) continue;
+      winner = t;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    res->has_solution = winner >= 0;
+    res->objective = winner >= 0 ? tbest[winner] : 0;
+    res->nodes = static_cast<int64_t>(hg.nodes);
+    res->fails = static_cast<int64_t>(hg.fails);
+    res->solutions = static_cast<int64_t>(hg.solutions);
+    res->iterations = static_cast<int64_t>(hg.iterations);
+    res->rows_evaluated = res->iterations * static_cast<int64_t>(m->n_t + m->n_rf + m->n_lin);
+    res->max_depth = hg.max_depth;
+    res->elapsed_ms = ms;
+    res->status = hg.limited ? PCCP_RES_LIMIT
+                             : (res->has_solution ? PCCP_RES_OPTIMAL : PCCP_RES_INFEASIBLE);
+    if (res->witness && winner >= 0) {
+      if (cudaMemcpyAsync(res->witness, d + o_w + static_cast<size_t>(winner) * m->n_vars * 4,
+                          static_cast<size_t>(m->n_vars) * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = PCCP_ERR_CUDA;
+        break;
+      }
+    }
+    if (hg.error == 1 || hg.error == 3) rc = PCCP_ERR_TIMEOUT;
+    if (hg.error == 2 || hg.error == 4) rc = PCCP_ERR_INVALID;
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(d, s);
+  if (rc != PCCP_OK) (void)cudaGetLastError();
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
 int pccp_solve(const pccp_model* m, const pccp_solve_opts* opts, pccp_result* result,
                void* stream) {
   if (!m || !opts || !result) return PCCP_ERR_INVALID;
-  if (!opts->deterministic) return PCCP_ERR_UNSUPPORTED;
+  if (opts->strategy != PCCP_INPUT_ORDER && opts->strategy != PCCP_FIRST_FAIL)
+    return PCCP_ERR_INVALID;
+  if (opts->mode != PCCP_OPTIMISE && opts->mode != PCCP_COUNT_ALL) return PCCP_ERR_INVALID;
+  if (!opts->deterministic) {
+    const int rc = check_device(m);
+    if (rc != PCCP_OK) return rc;
+    return solve_parallel(m, opts, result, static_cast<cudaStream_t>(stream));
+  }
   pccp_solve_opts o = *opts;
   if (o.threads <= 0) o.threads = 512;
   const pccp_model* one[1] = {m};

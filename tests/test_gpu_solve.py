@@ -75,3 +75,78 @@ def test_generic_models_search():
         om = oracle_model_from_lists(gm)
         same(pccp.solve(m), oracle.solve(om))
         same(pccp.solve(m, mode=pccp.PCCP_COUNT_ALL), oracle.solve(om, mode=oracle.COUNT_ALL))
+
+
+# ------------------------------------------- parallel search (EPS subproblems)
+
+from oracle import brute  # noqa: E402
+
+
+def _check_rcpsp_witness(inst, r):
+    n = inst.n
+    s = [int(v) for v in r["witness"][:n]]
+    assert brute.rcpsp_feasible(inst, s)
+    mk = max(s[i] + inst.durations[i] for i in range(n))
+    assert mk == r["objective"] == int(r["witness"][n + n * n])
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256])
+def test_parallel_tiny8_optima(threads):
+    for seed in range(0, 100, 7):
+        inst = config_instance("tiny8", seed)
+        r = pccp.solve(pccp.Model.from_rcpsp(inst), deterministic=False, threads=threads)
+        o = oracle.solve(rcpsp_model(inst))
+        assert r["status"] == pccp.PCCP_RES_OPTIMAL and r["objective"] == o["objective"]
+        _check_rcpsp_witness(inst, r)
+
+
+def test_parallel_count_all_and_proof_trees_are_exact():
+    """Without an incumbent the tree is fixed, so node, failure and solution
+    counts do not depend on how it is split among teams."""
+    for seed in range(0, 100, 11):
+        inst = config_instance("tiny8", seed)
+        m, om = pccp.Model.from_rcpsp(inst), rcpsp_model(inst)
+        opt = oracle.solve(om)["objective"]
+        c = oracle.solve(om, mode=oracle.COUNT_ALL, obj_ub=opt)
+        r = pccp.solve(m, mode=pccp.PCCP_COUNT_ALL, obj_ub=opt, deterministic=False)
+        assert (r["nodes"], r["fails"], r["solutions"]) == (c["nodes"], c["fails"], c["solutions"])
+        assert r["status"] == pccp.PCCP_RES_OPTIMAL
+        _check_rcpsp_witness(inst, r)
+        p = oracle.solve(om, obj_ub=opt - 1)
+        rp = pccp.solve(m, obj_ub=opt - 1, deterministic=False)
+        assert p["status"] == oracle.RES_INFEASIBLE and rp["status"] == pccp.PCCP_RES_INFEASIBLE
+        assert (rp["nodes"], rp["fails"]) == (p["nodes"], p["fails"])
+
+
+def test_parallel_generic_models():
+    for seed in range(30):
+        gm = draw_generic_model(9000 + seed, n_int=4, n_bool=3, dom=6)
+        m = pccp.Model.from_lists(gm.lb0, gm.ub0, gm.temporal, gm.linear, gm.reified,
+                                  gm.objective, gm.branch)
+        om = oracle_model_from_lists(gm)
+        o = oracle.solve(om)
+        r = pccp.solve(m, deterministic=False)
+        assert r["status"] == STATUS[o["status"]] and r["objective"] == o["objective"]
+        if o["has_solution"]:  # the witness is a solution: fixed, and stable under propagation
+            w = r["witness"]
+            assert all(w[v] == w[v] for v in gm.branch)
+            st, flb, fub, _ = oracle.propagate(om, w, w)
+            assert st == oracle.FIXPOINT
+        c = oracle.solve(om, mode=oracle.COUNT_ALL)
+        rc = pccp.solve(m, mode=pccp.PCCP_COUNT_ALL, deterministic=False)
+        assert (rc["nodes"], rc["solutions"]) == (c["nodes"], c["solutions"])
+
+
+def test_parallel_node_limited_j30():
+    """A budget of ~1,600 nodes per team lets depth-first dives (about 8
+    decisions per task) reach leaves; the limit is checked in batches of 64
+    nodes per team, so the count may exceed it by that much per team."""
+    inst = config_instance("j30", 0)
+    r = pccp.solve(pccp.Model.from_rcpsp(inst), deterministic=False, node_limit=2_000_000,
+                   time_limit_ms=20_000)
+    assert r["status"] in (pccp.PCCP_RES_LIMIT, pccp.PCCP_RES_OPTIMAL)
+    assert r["nodes"] >= 100_000 and r["has_solution"]
+    _check_rcpsp_witness(inst, r)
+    d = oracle.solve(rcpsp_model(inst), node_limit=2_000)  # the parallel search does better
+    if d["has_solution"]:
+        assert r["objective"] <= d["objective"]
