@@ -220,10 +220,10 @@ class ClockSampler:
 
 
 def launch_desc(args):
-    if not (args.team or args.teams or args.ctas_per_sm or args.linear_mode):
+    if not (args.team or args.teams or args.ctas_per_sm or args.skip_stable):
         return "library default"
     return {"team_threads": args.team, "teams_per_cta": args.teams,
-            "ctas_per_sm": args.ctas_per_sm, "linear_mode": args.linear_mode}
+            "ctas_per_sm": args.ctas_per_sm, "skip_stable": bool(args.skip_stable)}
 
 
 KERNEL_SOURCES = ("paper_2207_12116_gb300/csrc/k_propagate.cuh",
@@ -342,11 +342,12 @@ def run_gpu(args):
     ub = pristine_ub.clone()
     status = torch.empty(N_NODES, dtype=torch.int32, device=dev)
     iters = torch.empty(N_NODES, dtype=torch.int32, device=dev)
+    work = torch.empty((N_NODES, 2), dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     cfg = None
-    if args.team or args.teams or args.ctas_per_sm or args.linear_mode:
-        cfg = pccp.launch_config(args.team, args.teams, args.ctas_per_sm, 0, args.linear_mode)
+    if args.team or args.teams or args.ctas_per_sm or args.skip_stable:
+        cfg = pccp.launch_config(args.team, args.teams, args.ctas_per_sm, 0, args.skip_stable)
 
     def prepare():
         lb.copy_(pristine_lb)
@@ -372,7 +373,7 @@ def run_gpu(args):
     for k in range(args.steps):
         prepare()
         ev[k][0].record(stream)
-        pccp.propagate(model, lb, ub, status, iters, config=cfg)
+        pccp.propagate(model, lb, ub, status, iters, config=cfg, work=work)
         ev[k][1].record(stream)
     barrier()
     wall = time.perf_counter() - t_wall
@@ -383,9 +384,10 @@ def run_gpu(args):
 
     st = status.cpu().numpy()
     it = iters.cpu().numpy().astype(np.int64)
+    wk = work.cpu().numpy().astype(np.int64)
     rows_per_sweep = model.rows
-    evals = int(it.sum()) * rows_per_sweep
-    bytes_smem = int(it.sum()) * int(model.info.bytes_per_sweep)
+    evals = int(wk[:, 0].sum())          # rows actually evaluated (stable rows skipped)
+    bytes_smem = int(wk[:, 1].sum())     # algorithmic bytes they read
     io_bytes = 4 * nv * N_NODES * 4 + 8 * N_NODES  # read+write lb, ub; status, iterations
 
     e2e = None
@@ -438,6 +440,8 @@ def run_gpu(args):
                                                            "launch": launch_desc(args)}),
             "propagator_evals_per_s": world * evals / (ms_max / 1000),
             "fixpoint_iterations_per_node": float(it.mean()),
+            "rows_evaluated_per_node": evals / N_NODES,
+            "rows_skipped_fraction": 1.0 - evals / float(it.sum() * rows_per_sweep),
             "failed_nodes": int((st == 1).sum()),
             "roofline": {"bound": "smem", "achieved": achieved, "peak": smem_peak,
                          "unit": "GB/s", "frac": achieved / smem_peak if smem_peak else None,
@@ -477,7 +481,8 @@ def main():
     ap.add_argument("--team", type=int, default=0, help="threads per team (0: library default)")
     ap.add_argument("--teams", type=int, default=0, help="teams per CTA (0: library default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
-    ap.add_argument("--linear-mode", type=int, default=0, help="1 warp/row, 2 thread/row")
+    ap.add_argument("--skip-stable", action="store_true",
+                    help="re-run a row only after one of its variables changed")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

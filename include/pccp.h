@@ -145,14 +145,21 @@ typedef struct {
   int32_t teams_per_cta;  /* 1..15 (team_threads * teams_per_cta <= 1024) */
   int32_t ctas_per_sm;    /* cap on resident CTAs per SM used for the grid */
   int32_t max_iterations; /* per-store iteration budget (exceeded: PCCP_ERROR) */
-  int32_t linear_mode;    /* 0 default, 1 a warp per linear row, 2 a thread per row */
+  int32_t skip_stable;    /* 1: re-run a row only after one of its variables changed
+                             (change bitmaps per team; Sec. 6); 0: the eventless loop
+                             of Sec. 5.  Same fixed point either way. */
 } pccp_launch_config;
 
-/* pccp_propagate with an explicit launch shape (cfg may be NULL).  Returns
- * PCCP_ERR_SMEM if the requested teams do not fit shared memory. */
+/* pccp_propagate with an explicit launch shape (cfg may be NULL) and an
+ * optional work report: work is NULL or a DEVICE int32 [n_stores][2]
+ * receiving, per store, the rows evaluated and the algorithmic bytes they
+ * read (rows, operand bounds, change-tracking words).  Rows whose variables
+ * did not change since their last evaluation are not evaluated again
+ * (skipping stable propagators, Sec. 6); the fixed point is unchanged.
+ * Returns PCCP_ERR_SMEM if the requested teams do not fit shared memory. */
 int pccp_propagate_ex(const pccp_model* model, int32_t n_stores, int32_t* lb, int32_t* ub,
-                      int32_t* status, int32_t* iterations, const pccp_launch_config* cfg,
-                      void* stream);
+                      int32_t* status, int32_t* iterations, int32_t* work,
+                      const pccp_launch_config* cfg, void* stream);
 
 /* ---- search ------------------------------------------------------------ */
 
@@ -180,6 +187,8 @@ typedef struct {
   int64_t time_limit_ms; /* stop after this many ms of device time (<= 0: none) */
   int32_t threads;       /* threads per team (multiple of 32, <= 1024; 0 = auto) */
   int32_t blocks;        /* CTAs for the parallel search (0 = auto) */
+  int32_t skip_stable;   /* as in pccp_launch_config; also lets a left child run
+                            only the rows of the decided variable first */
 } pccp_solve_opts;
 
 /* Counters and outcome of one search.  A node is every store propagated,
@@ -197,7 +206,7 @@ typedef struct {
   int64_t fails;
   int64_t solutions;
   int64_t iterations;    /* fixed-point iterations summed over nodes */
-  int64_t rows_evaluated;/* iterations x rows: propagator evaluations */
+  int64_t rows_evaluated;/* propagator rows evaluated (stable rows are skipped) */
   int32_t max_depth;
   float elapsed_ms;      /* device time of the search kernel */
 } pccp_result;
@@ -215,6 +224,31 @@ int pccp_solve(const pccp_model* model, const pccp_solve_opts* opts, pccp_result
 int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
                      const pccp_solve_opts* opts, pccp_result* results, void* stream);
 
+/* ---- reusable batch, queued without synchronisation -------------------- */
+
+/* A batch of models prepared once for repeated searches (the batched
+ * configuration of the search: many models in one persistent launch).
+ * pccp_batch_create allocates and uploads the model descriptors and the
+ * result, witness and decision-stack buffers (synchronous); `threads` is the
+ * team size per model (0 = 256; a multiple of 32, <= 1024).  The models must
+ * outlive the batch.  Errors: INVALID, SMEM, CUDA. */
+typedef struct pccp_batch pccp_batch;
+int pccp_batch_create(const pccp_model* const* models, int32_t n_models, int32_t threads,
+                      pccp_batch** out);
+
+/* Queues one search of every model of the batch on `stream` (deterministic
+ * order, one team per model; same semantics and results as
+ * pccp_solve_batch).  Enqueues only a memset and one kernel launch: no host
+ * synchronisation and no allocation, so it may be captured in a CUDA graph
+ * and replayed.  Calls on one batch must not overlap on the GPU. */
+int pccp_batch_solve_async(pccp_batch* batch, const pccp_solve_opts* opts, void* stream);
+
+/* Synchronises `stream` and copies the last search's results (and the
+ * witnesses of results[i].witness != NULL) to the host; elapsed_ms is 0. */
+int pccp_batch_results(pccp_batch* batch, pccp_result* results, void* stream);
+
+void pccp_batch_destroy(pccp_batch* batch);
+
 /* ---- allocation-free batched solve ------------------------------------- */
 
 /* No counterpart in the paper.  Same contract and results as
@@ -226,7 +260,7 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
  * counter) is one fixed array of PCCP_NOALLOC_SCRATCH_BYTES in the library's
  * device memory; every GPU that loads the library holds it until the process
  * exits.  A request whose scratch does not fit returns PCCP_ERR_SCRATCH before
- * anything is queued: descriptors 40 B + results 56 B per model, 4 B per
+ * anything is queued: descriptors 40 B + results 64 B per model, 4 B per
  * variable of every model, and at least one decision stack of
  * (32 x max branch variables + 2) x 8 B.
  * The first call on a device looks up the array's device address (with that

@@ -24,7 +24,8 @@ from . import rcpsp  # noqa: F401
 
 __all__ = ["Model", "pccp_model_create", "pccp_model_destroy", "pccp_model_get_info",
            "pccp_propagate", "pccp_propagate_ex", "pccp_solve", "pccp_solve_batch",
-           "pccp_solve_batch_noalloc",
+           "pccp_solve_batch_noalloc", "pccp_batch_create", "pccp_batch_solve_async",
+           "pccp_batch_results", "pccp_batch_destroy", "Batch",
            "pccp_error_string", "propagate", "propagate_host", "solve", "solve_batch",
            "PccpError", "load", "library_path"]
 
@@ -63,9 +64,11 @@ def pccp_propagate(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr, stre
     return load().pccp_propagate(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr, stream)
 
 
-def pccp_propagate_ex(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr, cfg, stream):
+def pccp_propagate_ex(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr, work_ptr, cfg,
+                      stream):
     return load().pccp_propagate_ex(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr,
-                                    ctypes.byref(cfg) if cfg is not None else None, stream)
+                                    work_ptr, ctypes.byref(cfg) if cfg is not None else None,
+                                    stream)
 
 
 def pccp_solve(handle, opts, result, stream):
@@ -82,6 +85,26 @@ def pccp_solve_batch_noalloc(handles, opts, results, stream):
     n = len(handles)
     arr = (ctypes.c_void_p * n)(*[h.value for h in handles])
     return load().pccp_solve_batch_noalloc(arr, n, ctypes.byref(opts), results, stream)
+
+
+def pccp_batch_create(handles, threads):
+    n = len(handles)
+    arr = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    h = ctypes.c_void_p()
+    rc = load().pccp_batch_create(arr, n, threads, ctypes.byref(h))
+    return rc, h
+
+
+def pccp_batch_solve_async(handle, opts, stream):
+    return load().pccp_batch_solve_async(handle, ctypes.byref(opts), stream)
+
+
+def pccp_batch_results(handle, results, stream):
+    return load().pccp_batch_results(handle, results, stream)
+
+
+def pccp_batch_destroy(handle):
+    load().pccp_batch_destroy(handle)
 
 
 def pccp_error_string(code):
@@ -168,14 +191,17 @@ def _stream_ptr(stream):
 
 
 def launch_config(team_threads=0, teams_per_cta=0, ctas_per_sm=0, max_iterations=0,
-                  linear_mode=0):
+                  skip_stable=False):
     return _abi.pccp_launch_config(team_threads, teams_per_cta, ctas_per_sm, max_iterations,
-                                   linear_mode)
+                                   int(bool(skip_stable)))
 
 
-def propagate(model: Model, lb, ub, status=None, iterations=None, config=None, stream=None):
+def propagate(model: Model, lb, ub, status=None, iterations=None, config=None, stream=None,
+              work=None):
     """Propagate the stores in place.  lb/ub: int32 CUDA tensors [n, n_vars]
-    (contiguous).  Returns (status, iterations) int32 CUDA tensors [n]."""
+    (contiguous).  Returns (status, iterations) int32 CUDA tensors [n].
+    work: optional int32 CUDA tensor [n, 2] receiving, per store, the rows
+    evaluated and the algorithmic bytes they read."""
     import torch
     if lb.dtype != torch.int32 or ub.dtype != torch.int32 or not lb.is_cuda or not ub.is_cuda:
         raise PccpError(PCCP_ERR_INVALID, "lb/ub must be int32 CUDA tensors")
@@ -189,9 +215,10 @@ def propagate(model: Model, lb, ub, status=None, iterations=None, config=None, s
     if iterations is None:
         iterations = torch.empty(n, dtype=torch.int32, device=lb.device)
     sp = _stream_ptr(stream)
+    wp = ctypes.c_void_p(work.data_ptr()) if work is not None else ctypes.c_void_p(0)
     rc = pccp_propagate_ex(model.handle, n, ctypes.c_void_p(lb.data_ptr()),
                            ctypes.c_void_p(ub.data_ptr()), ctypes.c_void_p(status.data_ptr()),
-                           ctypes.c_void_p(iterations.data_ptr()), config, sp)
+                           ctypes.c_void_p(iterations.data_ptr()), wp, config, sp)
     check(rc, "pccp_propagate")
     return status, iterations
 
@@ -207,9 +234,10 @@ def propagate_host(model: Model, lb, ub, device="cuda", config=None, stream=None
     return out
 
 
-def _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks):
+def _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
+          skip_stable=False):
     return _abi.pccp_solve_opts(strategy, mode, int(bool(deterministic)), obj_ub, node_limit,
-                                time_limit_ms, threads, blocks)
+                                time_limit_ms, threads, blocks, int(bool(skip_stable)))
 
 
 def _result_dict(r, w):
@@ -222,8 +250,10 @@ def _result_dict(r, w):
 
 
 def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, deterministic=True,
-          obj_ub=INT32_MAX, node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None):
-    o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks)
+          obj_ub=INT32_MAX, node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None,
+          skip_stable=False):
+    o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
+              skip_stable)
     w = np.zeros(model.n_vars, dtype=np.int32)
     r = _abi.pccp_result()
     r.witness = w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
@@ -233,10 +263,12 @@ def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, determini
 
 
 def solve_batch(models, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
-                node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None, noalloc=False):
+                node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None, noalloc=False,
+                skip_stable=False):
     """Solve many models in one launch.  noalloc=True uses the allocation-free
     entry point (fixed device scratch; see include/pccp.h)."""
-    o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, threads, blocks)
+    o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, threads, blocks,
+              skip_stable)
     n = len(models)
     ws = [np.zeros(m.n_vars, dtype=np.int32) for m in models]
     res = (_abi.pccp_result * n)()
@@ -246,3 +278,39 @@ def solve_batch(models, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=IN
     rc = call([m.handle for m in models], o, res, _stream_ptr(stream))
     check(rc, call.__name__)
     return [_result_dict(res[i], ws[i]) for i in range(n)]
+
+
+class Batch:
+    """Models prepared for repeated batched searches; solve_async() only
+    queues work on the stream (capturable in a CUDA graph)."""
+
+    def __init__(self, models, threads=0):
+        self.models = list(models)  # keep the models alive
+        rc, h = pccp_batch_create([m.handle for m in self.models], threads)
+        check(rc, "pccp_batch_create")
+        self.handle = h
+        self._ws = [np.zeros(m.n_vars, dtype=np.int32) for m in self.models]
+
+    def solve_async(self, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
+                    node_limit=0, time_limit_ms=0, stream=None, skip_stable=False):
+        o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, 0, 0, skip_stable)
+        check(pccp_batch_solve_async(self.handle, o, _stream_ptr(stream)), "pccp_batch_solve_async")
+
+    def results(self, stream=None):
+        n = len(self.models)
+        res = (_abi.pccp_result * n)()
+        for i in range(n):
+            res[i].witness = self._ws[i].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        check(pccp_batch_results(self.handle, res, _stream_ptr(stream)), "pccp_batch_results")
+        return [_result_dict(res[i], self._ws[i]) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            pccp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

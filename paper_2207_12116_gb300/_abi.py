@@ -50,12 +50,13 @@ class pccp_model_info(ctypes.Structure):
 
 class pccp_launch_config(ctypes.Structure):
     _fields_ = [("team_threads", I32), ("teams_per_cta", I32), ("ctas_per_sm", I32),
-                ("max_iterations", I32), ("linear_mode", I32)]
+                ("max_iterations", I32), ("skip_stable", I32)]
 
 
 class pccp_solve_opts(ctypes.Structure):
     _fields_ = [("strategy", I32), ("mode", I32), ("deterministic", I32), ("obj_ub", I32),
-                ("node_limit", I64), ("time_limit_ms", I64), ("threads", I32), ("blocks", I32)]
+                ("node_limit", I64), ("time_limit_ms", I64), ("threads", I32), ("blocks", I32),
+                ("skip_stable", I32)]
 
 
 class pccp_result(ctypes.Structure):
@@ -71,12 +72,16 @@ SIGNATURES = {
     "pccp_model_destroy": (None, [P]),
     "pccp_model_get_info": (ctypes.c_int, [P, ctypes.POINTER(pccp_model_info)]),
     "pccp_propagate": (ctypes.c_int, [P, I32, P, P, P, P, P]),
-    "pccp_propagate_ex": (ctypes.c_int, [P, I32, P, P, P, P, ctypes.POINTER(pccp_launch_config), P]),
+    "pccp_propagate_ex": (ctypes.c_int, [P, I32, P, P, P, P, P, ctypes.POINTER(pccp_launch_config), P]),
     "pccp_solve": (ctypes.c_int, [P, ctypes.POINTER(pccp_solve_opts), ctypes.POINTER(pccp_result), P]),
     "pccp_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), I32, ctypes.POINTER(pccp_solve_opts),
                                         ctypes.POINTER(pccp_result), P]),
     "pccp_solve_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(P), I32, ctypes.POINTER(pccp_solve_opts),
                                                 ctypes.POINTER(pccp_result), P]),
+    "pccp_batch_create": (ctypes.c_int, [ctypes.POINTER(P), I32, I32, ctypes.POINTER(P)]),
+    "pccp_batch_solve_async": (ctypes.c_int, [P, ctypes.POINTER(pccp_solve_opts), P]),
+    "pccp_batch_results": (ctypes.c_int, [P, ctypes.POINTER(pccp_result), P]),
+    "pccp_batch_destroy": (None, [P]),
     "pccp_error_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
 

@@ -14,6 +14,7 @@ LIB = os.path.join(BUILD, "libpccp.so")
 SOURCES = [os.path.join(CSRC, "pccp.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "pccp_device.cuh"), os.path.join(CSRC, "k_propagate.cuh"),
                   os.path.join(CSRC, "pccp_noalloc.inc"),
+                  os.path.join(CSRC, "pccp_batch.inc"), os.path.join(CSRC, "k_solve_eps.cuh"),
                   os.path.join(ROOT, "include", "pccp.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -17,6 +17,7 @@ struct PropArgs {
   int32_t* ub;
   int32_t* status;
   int32_t* iters;
+  int32_t* work;  // [n_stores][2] {rows evaluated, algorithmic bytes} or null
   int* counter;
   uint32_t image_bytes;
   int n_vars;
@@ -24,18 +25,28 @@ struct PropArgs {
   int team_size;
   int teams;
   int max_iter;
-  int linear_mode;
+  int track_words;
+};
+
+// Per-team scalars of k_propagate (shared memory).
+struct PropCtrl {
+  int next;
+  int pad[3];
+  FixCtrl fc;
 };
 
 // Instantiated for 1024-thread CTAs (one per SM) and for CTAs of up to 512
 // threads with three resident per SM (registers capped for 48 warps/SM).
-template <int kMaxThreads, int kMinBlocks>
+template <int kMaxThreads, int kMinBlocks, bool kTrack>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t* img = smem;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + a.image_bytes);
-  int* ctrl_base = reinterpret_cast<int*>(smem + a.image_bytes + 16);
-  int2* st_base = reinterpret_cast<int2*>(smem + a.image_bytes + 16 + 16 * a.teams);
+  PropCtrl* ctrl_base = reinterpret_cast<PropCtrl*>(smem + a.image_bytes + 16);
+  const int tw16 = (a.track_words + 3) & ~3;  // words, 16-byte multiple
+  uint32_t* track_base =
+      reinterpret_cast<uint32_t*>(smem + a.image_bytes + 16 + sizeof(PropCtrl) * a.teams);
+  int2* st_base = reinterpret_cast<int2*>(track_base + static_cast<size_t>(tw16) * a.teams);
 
   if (threadIdx.x == 0) mbar_init(mbar, 1);
   const bool ok = load_image(img, a.image, a.image_bytes, mbar, 0);
@@ -48,20 +59,26 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   tm.lane = threadIdx.x & 31;
   tm.warp = tm.tid >> 5;
   tm.nwarps = a.team_size >> 5;
-  int* ctrl = ctrl_base + 4 * team_id;  // [0] next store, [1] failure flag
+  PropCtrl* ctrl = ctrl_base + team_id;
   int2* st = st_base + static_cast<size_t>(team_id) * a.n_vars;
   const Tab tb = make_tab(img);
+  const Track tk = make_track(track_base + static_cast<size_t>(tw16) * team_id, tb.n_vars,
+                              tb.n_lin + tb.n_lin_long);
   const int nv = a.n_vars;
 
   for (;;) {
-    if (tm.tid == 0) ctrl[0] = atomicAdd(a.counter, 1);
+    if (tm.tid == 0) ctrl->next = atomicAdd(a.counter, 1);
     team_bar(tm.bar, tm.nthr);
-    const int s = ctrl[0];
+    const int s = ctrl->next;
     if (s >= a.n_stores) break;
     if (!ok) {  // table never arrived: report the stores this team takes
       if (tm.tid == 0) {
         a.status[s] = kError;
         if (a.iters) a.iters[s] = 0;
+        if (a.work) {
+          a.work[2 * static_cast<size_t>(s)] = 0;
+          a.work[2 * static_cast<size_t>(s) + 1] = 0;
+        }
       }
       continue;
     }
@@ -74,10 +91,15 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
       st[v] = make_int2(l, u);
       empty |= l > u;
     }
-    if (tm.tid == 0) ctrl[1] = 0;
+    if (kTrack) track_clear02(tk, tm);
+    if (tm.tid == 0) {
+      ctrl->fc.fail = 0;
+      ctrl->fc.evals = 0;
+      ctrl->fc.bytes = 0;
+    }
     const bool any_empty = team_bar_or(tm.bar, tm.nthr, empty);
     int status = kFailed, it = 0;
-    if (!any_empty) status = team_fixpoint(tb, st, tm, &ctrl[1], a.max_iter, it, a.linear_mode);
+    if (!any_empty) status = team_fixpoint<kTrack>(tb, st, tm, &ctrl->fc, tk, true, a.max_iter, it);
     for (int v = tm.tid; v < nv; v += tm.nthr) {
       const int2 D = st[v];
       lbs[v] = D.x;
@@ -86,6 +108,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
     if (tm.tid == 0) {
       a.status[s] = status;
       if (a.iters) a.iters[s] = it;
+      if (a.work) {
+        a.work[2 * static_cast<size_t>(s)] = ctrl->fc.evals;
+        a.work[2 * static_cast<size_t>(s) + 1] = ctrl->fc.bytes;
+      }
     }
   }
 }

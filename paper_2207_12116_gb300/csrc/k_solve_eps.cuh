@@ -23,7 +23,7 @@ struct EpsGlobal {
   int error;     // 1 iteration budget, 2 decision stack, 3 table load, 4 frontier overflow
   unsigned long long t0;          // globaltimer at the first node (0 until set)
   unsigned long long live_nodes;  // node count published in batches, for the limit
-  unsigned long long nodes, fails, solutions, iterations;
+  unsigned long long nodes, fails, solutions, iterations, evals;
   int max_depth;
   int pad[3];
 };
@@ -52,21 +52,21 @@ struct EpsArgs {
   int mode;
   int strategy;
   int obj_ub;
-  int linear_mode;
+  int track_words;
   int64_t node_limit;
   int64_t time_limit_ns;
 };
 
 struct EpsCtrl {
   unsigned long long sel[2];
-  int fail;
+  FixCtrl fc;
   int stop;
   int record;
   int err;
   int depth;
   int next;
   int out;
-  int pad[5];
+  int pad[2];
 };
 
 enum : int { kNodeFailed = 0, kNodeSolution = 1, kNodeBranch = 2, kNodeStop = 3, kNodeError = 4 };
@@ -89,9 +89,10 @@ __device__ __forceinline__ uint64_t eps_now_ns() {
 // the selection key (branch index in the low 32 bits).  Team-uniform result.
 // Broadcast slots follow the protocol of team_dfs: written before a barrier,
 // read after it, not rewritten before another barrier has passed.
+template <bool kTrack>
 __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm, EpsCtrl* sc,
-                                        unsigned par, const EpsArgs& a, int& it,
-                                        unsigned long long& key) {
+                                        const Track& tk, bool seeded, unsigned par,
+                                        const EpsArgs& a, int& it, unsigned long long& key) {
   EpsGlobal* g = a.g;
   if (tm.tid == 0) {
     int stop = ld_relaxed_gpu(&g->stop);
@@ -109,15 +110,20 @@ __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm,
         const int gb = ld_relaxed_gpu(&g->best);
         if (gb != INT_MAX) bound = min(bound, gb - 1);
       }
-      if (bound < INT_MAX) atom_min_s32(&st[tb.objective].y, bound);
+      if (bound < INT_MAX) {
+        const int old = atom_min_s32(&st[tb.objective].y, bound);
+        if (kTrack && old > bound) mark_changed(tb, tk, 2, tb.objective);
+      }
     }
     sc->stop = stop;
-    sc->fail = 0;
+    sc->fc.fail = 0;
+    sc->fc.evals = 0;
+    sc->fc.bytes = 0;
     sc->sel[par] = ~0ull;
   }
   team_bar(tm.bar, tm.nthr);
   if (sc->stop) return kNodeStop;
-  const int fst = team_fixpoint(tb, st, tm, &sc->fail, a.max_iter, it, a.linear_mode);
+  const int fst = team_fixpoint<kTrack>(tb, st, tm, &sc->fc, tk, !seeded, a.max_iter, it);
   if (fst == kError) return kNodeError;
   if (fst == kFailed) return kNodeFailed;
   unsigned long long* sel = &sc->sel[par];
@@ -132,6 +138,7 @@ __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm,
       if (a.strategy == PCCP_INPUT_ORDER) break;
     }
   }
+  if (kTrack) track_clear02(tk, tm);  // for a left child's seeded fixed point
   team_bar(tm.bar, tm.nthr);
   key = *sel;
   return key == ~0ull ? kNodeSolution : kNodeBranch;
@@ -170,9 +177,11 @@ __device__ __forceinline__ void eps_solution(const Tab& tb, int2* st, const Team
   }
 }
 
+template <bool kTrack>
 __device__ __forceinline__ void eps_restore(const int2* root, int2* st, const Team& tm, int nv,
-                                            const int2* path, int len) {
+                                            const Track& tk, const int2* path, int len) {
   for (int v = tm.tid; v < nv; v += tm.nthr) st[v] = __ldg(root + v);
+  if (kTrack) track_clear02(tk, tm);
   team_bar(tm.bar, tm.nthr);
   for (int k = tm.tid; k < len; k += tm.nthr) {
     const int2 e = path[k];
@@ -201,6 +210,7 @@ struct EpsSmem {
   uint8_t* img;
   uint64_t* mbar;
   EpsCtrl* sc;
+  uint32_t* track;
   int2* st;
 };
 
@@ -210,7 +220,11 @@ __device__ __forceinline__ EpsSmem eps_smem(uint8_t* smem, const EpsArgs& a, int
   s.mbar = reinterpret_cast<uint64_t*>(smem + a.image_bytes);
   EpsCtrl* ctrl = reinterpret_cast<EpsCtrl*>(smem + a.image_bytes + 16);
   s.sc = ctrl + team_id;
-  int2* st_base = reinterpret_cast<int2*>(smem + a.image_bytes + 16 + sizeof(EpsCtrl) * a.teams);
+  const int tw16 = (a.track_words + 3) & ~3;
+  uint32_t* track_base =
+      reinterpret_cast<uint32_t*>(smem + a.image_bytes + 16 + sizeof(EpsCtrl) * a.teams);
+  s.track = track_base + static_cast<size_t>(tw16) * team_id;
+  int2* st_base = reinterpret_cast<int2*>(track_base + static_cast<size_t>(tw16) * a.teams);
   s.st = st_base + static_cast<size_t>(team_id) * a.n_vars;
   return s;
 }
@@ -229,6 +243,7 @@ __device__ __forceinline__ Team eps_team(const EpsArgs& a, int team_id) {
 // One breadth-first level: every input path is propagated once; failures
 // and solutions are counted; every other node pushes its two children
 // (left ub <= m, right lb >= m + 1) to the output level.
+template <bool kTrack>
 __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
@@ -242,9 +257,10 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
     atomicCAS(&a.g->t0, 0ull, static_cast<unsigned long long>(eps_now_ns()));
   const Team tm = eps_team(a, team_id);
   const Tab tb = make_tab(sm.img);
+  const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
   EpsCtrl* sc = sm.sc;
-  unsigned long long nodes = 0, published = 0, fails = 0, sols = 0, iters = 0;
+  unsigned long long nodes = 0, published = 0, fails = 0, sols = 0, iters = 0, evals = 0;
   int max_d = 0;
   unsigned par = 0;
   for (;;) {
@@ -253,15 +269,16 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
     const int p = sc->next;
     if (p >= a.n_in) break;
     const int2* path = a.in_paths + static_cast<size_t>(p) * a.in_len;
-    eps_restore(a.root, sm.st, tm, a.n_vars, path, a.in_len);
+    eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, tk, path, a.in_len);
     int it = 0;
     unsigned long long key = 0;
-    const int r = eps_node(tb, sm.st, tm, sc, par, a, it, key);
+    const int r = eps_node<kTrack>(tb, sm.st, tm, sc, tk, false, par, a, it, key);
     par ^= 1u;
     if (r == kNodeStop) break;
     if (tm.tid == 0) {
       eps_count_node(a, nodes, published);
       iters += it;
+      evals += sc->fc.evals;
       max_d = max(max_d, a.in_len);
     }
     if (r == kNodeError) {
@@ -308,11 +325,13 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
     atomicAdd(&a.g->fails, fails);
     atomicAdd(&a.g->solutions, sols);
     atomicAdd(&a.g->iterations, iters);
+    atomicAdd(&a.g->evals, evals);
     atomicMax(&a.g->max_depth, max_d);
   }
 }
 
 // Persistent teams search the subtrees under the frontier paths depth first.
+template <bool kTrack>
 __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
@@ -326,11 +345,12 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
     atomicCAS(&a.g->t0, 0ull, static_cast<unsigned long long>(eps_now_ns()));
   const Team tm = eps_team(a, team_id);
   const Tab tb = make_tab(sm.img);
+  const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
   EpsCtrl* sc = sm.sc;
   int2* stack = a.stacks + static_cast<size_t>(team_gid) * a.max_depth;
   const int base = a.in_len;
-  unsigned long long nodes = 0, published = 0, fails = 0, sols = 0, iters = 0;
+  unsigned long long nodes = 0, published = 0, fails = 0, sols = 0, iters = 0, evals = 0;
   int max_d = 0;
   unsigned par = 0;
   bool done = false;
@@ -342,11 +362,12 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
     const int2* path = a.in_paths + static_cast<size_t>(p) * base;
     for (int k = tm.tid; k < base; k += tm.nthr) stack[k] = path[k];
     int depth = base;  // thread 0's copy is authoritative
-    eps_restore(a.root, sm.st, tm, a.n_vars, path, base);
+    eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, tk, path, base);
+    bool seeded = false;  // team-uniform
     for (;;) {
       int it = 0;
       unsigned long long key = 0;
-      const int r = eps_node(tb, sm.st, tm, sc, par, a, it, key);
+      const int r = eps_node<kTrack>(tb, sm.st, tm, sc, tk, seeded, par, a, it, key);
       par ^= 1u;
       if (r == kNodeStop) {
         done = true;
@@ -355,6 +376,7 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
       if (tm.tid == 0) {
         eps_count_node(a, nodes, published);
         iters += it;
+        evals += sc->fc.evals;
         max_d = max(max_d, depth);
       }
       if (r == kNodeError) {
@@ -374,7 +396,8 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
             const int m = D.x + (D.y - D.x) / 2;
             stack[depth] = make_int2(v, m);
             ++depth;
-            atom_min_s32(&sm.st[v].y, m);
+            atom_min_s32(&sm.st[v].y, m);  // m < ub(v): always a change
+            if (kTrack) mark_changed(tb, tk, 2, v);
           }
           sc->err = err;
         }
@@ -383,6 +406,7 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
           done = true;
           break;
         }
+        seeded = true;
         continue;
       }
       if (r == kNodeFailed) {
@@ -405,7 +429,8 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
       team_bar(tm.bar, tm.nthr);
       const int d = sc->depth;
       if (d < 0) break;  // subtree exhausted: next subproblem
-      eps_restore(a.root, sm.st, tm, a.n_vars, stack, d);
+      eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, tk, stack, d);
+      seeded = false;
     }
   }
   if (tm.tid == 0) {
@@ -413,6 +438,7 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
     atomicAdd(&a.g->fails, fails);
     atomicAdd(&a.g->solutions, sols);
     atomicAdd(&a.g->iterations, iters);
+    atomicAdd(&a.g->evals, evals);
     atomicMax(&a.g->max_depth, max_d);
   }
 }

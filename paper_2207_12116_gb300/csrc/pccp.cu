@@ -32,7 +32,6 @@ using namespace pccp;
 namespace {
 
 constexpr int kDefaultMaxIter = 1 << 24;
-constexpr int kDefaultLinearMode = 1;  // a thread per linear row
 constexpr int kMaxTeamsPerCta = 15;  // named barriers 1..15
 constexpr int32_t kValueLimit = (1 << 30) - 1;
 
@@ -58,11 +57,12 @@ struct InstanceDesc {
 struct InstanceResult {
   int32_t status, has_solution, objective, max_depth;
   int64_t nodes, fails, solutions, iterations;
+  int64_t evals;
   int32_t error, pad;
 };
 
 static_assert(sizeof(InstanceDesc) == 40, "descriptor size is part of the scratch accounting");
-static_assert(sizeof(InstanceResult) == 56, "result size is part of the scratch accounting");
+static_assert(sizeof(InstanceResult) == 64, "result size is part of the scratch accounting");
 
 struct SolveArgs {
   const InstanceDesc* inst;
@@ -75,10 +75,10 @@ struct SolveArgs {
   int mode;
   int strategy;
   int obj_ub;
-  int linear_mode;
   int64_t node_limit;
   int64_t time_limit_ns;
   uint32_t max_image_bytes;
+  int max_track_words;
 };
 
 // Broadcast slots of one team's search.  Each slot has one writer (thread 0)
@@ -86,13 +86,13 @@ struct SolveArgs {
 // follows the write and is not rewritten before another barrier has passed.
 struct SearchCtrl {
   unsigned long long sel[2];  // selection key, one slot per node parity
-  int fail;    // fixed-point failure flag (reset in P1, set by any thread)
+  FixCtrl fc;  // fixed-point failure flag and work counters (reset in P1)
   int stop;    // P1: limit reached
   int record;  // solution path: copy the witness
   int err;     // branch path: decision stack overflow
   int depth;   // backtrack: new depth, -1 when the tree is exhausted
   int next;    // next model index (CTA loop)
-  int pad[6];
+  int pad[2];
 };
 
 constexpr unsigned long long kNoVar = ~0ull;
@@ -104,18 +104,23 @@ constexpr uint32_t kRightBit = 0x80000000u;
 // All control decisions are made by thread 0 and broadcast through shared
 // memory; every broadcast slot is written before a barrier and read after it,
 // and never rewritten before the next barrier that follows all its reads.
+template <bool kTrack>
 __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st, const Team& tm,
-                         SearchCtrl* sc, int2* stack, const SolveArgs& a, int max_iter,
-                         int32_t* witness, InstanceResult* out) {
+                         SearchCtrl* sc, const Track& tk, int2* stack, const SolveArgs& a,
+                         int max_iter, int32_t* witness, InstanceResult* out) {
   const int nv = tb.n_vars;
   const uint64_t t0 = globaltimer_ns();
   // thread-0 state
-  int64_t nodes = 0, fails = 0, sols = 0, iters = 0;
+  int64_t nodes = 0, fails = 0, sols = 0, iters = 0, evals = 0;
   int depth = 0, max_d = 0, best = 0, objective = 0, error = 0;
   bool has_sol = false, limited = false, satisfied = false;
   unsigned par = 0;
+  // team-uniform: the store is a fixed point strengthened by marked tells
+  // (left descent) rather than a store built from the root
+  bool seeded = false;
 
   for (int v = tm.tid; v < nv; v += tm.nthr) st[v] = __ldg(root + v);
+  if (kTrack) track_clear02(tk, tm);
 
   for (;;) {
     // P1: limits, objective bound, reset of per-node slots
@@ -127,20 +132,26 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
       if (!stop && tb.objective >= 0) {
         int bound = a.obj_ub;
         if (a.mode == PCCP_OPTIMISE && has_sol) bound = min(bound, best - 1);
-        if (bound < INT_MAX) atom_min_s32(&st[tb.objective].y, bound);
+        if (bound < INT_MAX) {
+          const int old = atom_min_s32(&st[tb.objective].y, bound);
+          if (kTrack && old > bound) mark_changed(tb, tk, 2, tb.objective);
+        }
       }
       limited = stop != 0;
       sc->stop = stop;
-      sc->fail = 0;
+      sc->fc.fail = 0;
+      sc->fc.evals = 0;
+      sc->fc.bytes = 0;
       sc->sel[par] = kNoVar;
     }
     team_bar(tm.bar, tm.nthr);  // N1
     if (sc->stop) break;
     int it = 0;
-    const int fst = team_fixpoint(tb, st, tm, &sc->fail, max_iter, it, a.linear_mode);
+    const int fst = team_fixpoint<kTrack>(tb, st, tm, &sc->fc, tk, !seeded, max_iter, it);
     if (tm.tid == 0) {
       ++nodes;
       iters += it;
+      evals += sc->fc.evals;
       max_d = max(max_d, depth);
     }
     if (fst == kError) {
@@ -167,6 +178,7 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
           if (a.strategy == PCCP_INPUT_ORDER) break;
         }
       }
+      if (kTrack) track_clear02(tk, tm);  // for a left child's seeded fixed point
       team_bar(tm.bar, tm.nthr);  // N2
       const unsigned long long key = *sel;
       if (key == kNoVar) {  // every branch variable fixed: a solution
@@ -196,7 +208,8 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
           } else {
             stack[depth] = make_int2(v, m);  // left: ub(v) <= m
             ++depth;
-            atom_min_s32(&st[v].y, m);
+            atom_min_s32(&st[v].y, m);  // m < ub(v): always a change
+            if (kTrack) mark_changed(tb, tk, 2, v);
           }
           sc->err = error != 0;
         }
@@ -205,6 +218,7 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
           if (tm.tid == 0) limited = true;
           break;
         }
+        seeded = true;
       }
     }
     par ^= 1u;
@@ -224,6 +238,8 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
       const int d = sc->depth;
       if (d < 0) break;
       for (int v = tm.tid; v < nv; v += tm.nthr) st[v] = __ldg(root + v);
+      if (kTrack) track_clear02(tk, tm);
+      seeded = false;
       team_bar(tm.bar, tm.nthr);  // N5
       for (int k = tm.tid; k < d; k += tm.nthr) {
         const int2 e = stack[k];
@@ -244,16 +260,20 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
     out->fails = fails;
     out->solutions = sols;
     out->iterations = iters;
+    out->evals = evals;
     out->error = error;
   }
 }
 
+template <bool kTrack>
 __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t* img = smem;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + a.max_image_bytes);
   SearchCtrl* sc = reinterpret_cast<SearchCtrl*>(smem + a.max_image_bytes + 16);
-  int2* st = reinterpret_cast<int2*>(smem + a.max_image_bytes + 16 + sizeof(SearchCtrl));
+  uint32_t* track_base =
+      reinterpret_cast<uint32_t*>(smem + a.max_image_bytes + 16 + sizeof(SearchCtrl));
+  int2* st = reinterpret_cast<int2*>(track_base + ((a.max_track_words + 3) & ~3));
   if (threadIdx.x == 0) mbar_init(mbar, 1);
   Team tm;
   tm.tid = threadIdx.x;
@@ -280,7 +300,9 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
     }
     parity ^= 1u;
     const Tab tb = make_tab(img);
-    team_dfs(tb, d.root, st, tm, sc, stack, a, d.max_iter, a.witness + d.witness_off, &a.res[i]);
+    const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
+    team_dfs<kTrack>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter, a.witness + d.witness_off,
+                     &a.res[i]);
   }
 }
 
@@ -334,8 +356,12 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
     if (!in_range(d->branch_vars[k])) return PCCP_ERR_INVALID;
 
   std::vector<uint2> T, RF;
-  std::vector<int4> L;
-  std::vector<uint32_t> TERMS;
+  struct LinRow {
+    int32_t c;
+    std::vector<uint32_t> terms;
+  };
+  std::vector<LinRow> short_rows, long_rows;
+  int32_t n_terms = 0;
   int64_t bytes_per_sweep = 0;
   for (int32_t i = 0; i < d->n_temporal; ++i) {
     const int32_t x = d->temporal[3 * i], y = d->temporal[3 * i + 1], dd = d->temporal[3 * i + 2];
@@ -368,7 +394,8 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
     if (o1 > o0 && (!d->term_coef || !d->term_var)) return PCCP_ERR_INVALID;
     const int64_t c = d->linear_c[i];
     int64_t sum = 0, mx = 0;
-    const int32_t first = static_cast<int32_t>(TERMS.size());
+    LinRow row;
+    row.c = static_cast<int32_t>(c);
     for (int32_t k = o0; k < o1; ++k) {
       const int32_t a = d->term_coef[k], v = d->term_var[k];
       if (!in_range(v)) return PCCP_ERR_INVALID;
@@ -376,14 +403,59 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
       if (a < -32768 || a > 32767) return PCCP_ERR_UNSUPPORTED;
       sum += iabs64(a) * B[v];
       mx = std::max(mx, iabs64(a) * B[v]);
-      TERMS.push_back(static_cast<uint32_t>(v) |
-                      (static_cast<uint32_t>(static_cast<uint16_t>(a)) << 16));
+      row.terms.push_back(static_cast<uint32_t>(v) |
+                          (static_cast<uint32_t>(static_cast<uint16_t>(a)) << 16));
     }
-    const int32_t len = static_cast<int32_t>(TERMS.size()) - first;
+    const int32_t len = static_cast<int32_t>(row.terms.size());
     if (len == 0) return PCCP_ERR_INVALID;
     if (iabs64(c) + 2 * sum + 2 * mx > static_cast<int64_t>(INT32_MAX)) return PCCP_ERR_OVERFLOW;
-    L.push_back(make_int4(static_cast<int32_t>(c), first, len, 0));
     bytes_per_sweep += 12 + 12 * static_cast<int64_t>(len);
+    n_terms += len;
+    (len <= kShortRow ? short_rows : long_rows).push_back(std::move(row));
+  }
+  // Short rows: longest first so each 32-row tile holds rows of similar
+  // length; tiles transposed (term t of lane l at tile start + 32 t + l).
+  std::stable_sort(short_rows.begin(), short_rows.end(), [](const LinRow& p, const LinRow& q) {
+    return p.terms.size() > q.terms.size();
+  });
+  std::vector<int4> L, LL;
+  std::vector<uint32_t> TERMS, TERMS_LONG;
+  for (size_t t0 = 0; t0 < short_rows.size(); t0 += 32) {
+    const size_t t1 = std::min(short_rows.size(), t0 + 32);
+    size_t maxlen = 0;
+    for (size_t r = t0; r < t1; ++r) maxlen = std::max(maxlen, short_rows[r].terms.size());
+    const size_t tile = TERMS.size();
+    TERMS.resize(tile + 32 * maxlen, 0u);
+    for (size_t r = t0; r < t1; ++r) {
+      const LinRow& row = short_rows[r];
+      const size_t lane = r - t0;
+      for (size_t k = 0; k < row.terms.size(); ++k) TERMS[tile + 32 * k + lane] = row.terms[k];
+      L.push_back(make_int4(row.c, static_cast<int32_t>(tile + lane),
+                            static_cast<int32_t>(row.terms.size()), 0));
+    }
+  }
+  for (const LinRow& row : long_rows) {
+    LL.push_back(make_int4(row.c, static_cast<int32_t>(TERMS_LONG.size()),
+                           static_cast<int32_t>(row.terms.size()), 0));
+    TERMS_LONG.insert(TERMS_LONG.end(), row.terms.begin(), row.terms.end());
+  }
+  // variable -> linear rows holding it (short rows 0.., long rows |L|..),
+  // used to mark the rows to run again after the variable changes
+  std::vector<std::vector<int32_t>> by_var(nv);
+  auto add_row = [&by_var](const std::vector<uint32_t>& terms, int32_t r) {
+    for (uint32_t t : terms) {
+      std::vector<int32_t>& rows = by_var[t & 0xffffu];
+      if (rows.empty() || rows.back() != r) rows.push_back(r);
+    }
+  };
+  for (size_t r = 0; r < short_rows.size(); ++r)
+    add_row(short_rows[r].terms, static_cast<int32_t>(r));
+  for (size_t r = 0; r < long_rows.size(); ++r)
+    add_row(long_rows[r].terms, static_cast<int32_t>(short_rows.size() + r));
+  std::vector<int32_t> ADJ_OFF(nv + 1, 0), ADJ;
+  for (int64_t v = 0; v < nv; ++v) {
+    ADJ.insert(ADJ.end(), by_var[v].begin(), by_var[v].end());
+    ADJ_OFF[v + 1] = static_cast<int32_t>(ADJ.size());
   }
 
   TableHeader h;
@@ -392,7 +464,8 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   h.n_t = static_cast<int32_t>(T.size());
   h.n_rf = static_cast<int32_t>(RF.size());
   h.n_lin = static_cast<int32_t>(L.size());
-  h.n_terms = static_cast<int32_t>(TERMS.size());
+  h.n_lin_long = static_cast<int32_t>(LL.size());
+  h.n_terms = n_terms;
   h.n_branch = d->n_branch;
   h.objective = d->objective;
   size_t off = sizeof(TableHeader);
@@ -404,8 +477,17 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   off = align16(off + L.size() * sizeof(int4));
   h.off_terms = static_cast<int32_t>(off);
   off = align16(off + TERMS.size() * sizeof(uint32_t));
+  h.off_lin_long = static_cast<int32_t>(off);
+  off = align16(off + LL.size() * sizeof(int4));
+  h.off_terms_long = static_cast<int32_t>(off);
+  off = align16(off + TERMS_LONG.size() * sizeof(uint32_t));
   h.off_branch = static_cast<int32_t>(off);
   off = align16(off + static_cast<size_t>(d->n_branch) * sizeof(int32_t));
+  h.off_adj_off = static_cast<int32_t>(off);
+  off = align16(off + ADJ_OFF.size() * sizeof(int32_t));
+  h.off_adj = static_cast<int32_t>(off);
+  h.n_adj = static_cast<int32_t>(ADJ.size());
+  off = align16(off + ADJ.size() * sizeof(int32_t));
   if (off > (1u << 30)) return PCCP_ERR_UNSUPPORTED;
   h.image_bytes = static_cast<int32_t>(off);
 
@@ -416,18 +498,33 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   if (!L.empty()) std::memcpy(p->image.data() + h.off_lin, L.data(), L.size() * sizeof(int4));
   if (!TERMS.empty())
     std::memcpy(p->image.data() + h.off_terms, TERMS.data(), TERMS.size() * sizeof(uint32_t));
+  if (!LL.empty()) std::memcpy(p->image.data() + h.off_lin_long, LL.data(), LL.size() * sizeof(int4));
+  if (!TERMS_LONG.empty())
+    std::memcpy(p->image.data() + h.off_terms_long, TERMS_LONG.data(),
+                TERMS_LONG.size() * sizeof(uint32_t));
   if (d->n_branch > 0)
     std::memcpy(p->image.data() + h.off_branch, d->branch_vars,
                 static_cast<size_t>(d->n_branch) * sizeof(int32_t));
+  std::memcpy(p->image.data() + h.off_adj_off, ADJ_OFF.data(), ADJ_OFF.size() * sizeof(int32_t));
+  if (!ADJ.empty())
+    std::memcpy(p->image.data() + h.off_adj, ADJ.data(), ADJ.size() * sizeof(int32_t));
   p->n_vars = h.n_vars;
   p->n_t = h.n_t;
   p->n_rf = h.n_rf;
-  p->n_lin = h.n_lin;
+  p->n_lin = h.n_lin + h.n_lin_long;
   p->n_terms = h.n_terms;
   p->n_branch = h.n_branch;
   p->objective = h.objective;
   p->bytes_per_sweep = bytes_per_sweep;
   return PCCP_OK;
+}
+
+// Shared memory of k_solve: table image, mbarrier, control, change
+// tracking, one store.
+size_t solve_smem(uint32_t max_img, int max_track_words, int max_vars) {
+  return static_cast<size_t>(max_img) + 16 + sizeof(SearchCtrl) +
+         4 * static_cast<size_t>((max_track_words + 3) & ~3) +
+         static_cast<size_t>(max_vars) * sizeof(int2);
 }
 
 int max_dyn_smem() {
@@ -472,18 +569,22 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
   int team = (cfg && cfg->team_threads > 0) ? cfg->team_threads : 128;
   if (team % 32 != 0 || team > 1024) return PCCP_ERR_INVALID;
-  if (cfg && (cfg->linear_mode < 0 || cfg->linear_mode > 2)) return PCCP_ERR_INVALID;
   const size_t base = static_cast<size_t>(m->image_bytes) + 16;
-  const size_t per_team = 16 + static_cast<size_t>(m->n_vars) * sizeof(int2);
+  const size_t per_team = sizeof(PropCtrl) + 4 * ((track_words(m->n_vars, m->n_lin) + 3) & ~3) +
+                          static_cast<size_t>(m->n_vars) * sizeof(int2);
   if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
-  int teams = (cfg && cfg->teams_per_cta > 0) ? cfg->teams_per_cta : 8;
+  // default: 4 teams of 128 threads per CTA, three CTAs per SM (48 warps)
+  int teams = (cfg && cfg->teams_per_cta > 0) ? cfg->teams_per_cta : 4;
   if (teams > kMaxTeamsPerCta) return PCCP_ERR_INVALID;
   teams = std::min({teams, fit, 1024 / team});
   if (cfg && cfg->teams_per_cta > 0 && teams < cfg->teams_per_cta) return PCCP_ERR_SMEM;
   if (teams < 1) return PCCP_ERR_SMEM;
   const size_t smem = base + static_cast<size_t>(teams) * per_team;
-  const auto kern = (teams * team <= 512) ? k_propagate<512, 3> : k_propagate<1024, 1>;
+  const bool track = cfg && cfg->skip_stable;
+  const auto kern = (teams * team <= 512)
+                        ? (track ? k_propagate<512, 3, true> : k_propagate<512, 3, false>)
+                        : (track ? k_propagate<1024, 1, true> : k_propagate<1024, 1, false>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -599,8 +700,8 @@ int pccp_model_get_info(const pccp_model* m, pccp_model_info* info) {
 }
 
 int pccp_propagate_ex(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_t* ub,
-                      int32_t* status, int32_t* iterations, const pccp_launch_config* cfg,
-                      void* stream) {
+                      int32_t* status, int32_t* iterations, int32_t* work,
+                      const pccp_launch_config* cfg, void* stream) {
   if (!m || n_stores < 0) return PCCP_ERR_INVALID;
   if (n_stores == 0) return PCCP_OK;
   if (!lb || !ub || !status) return PCCP_ERR_INVALID;
@@ -627,7 +728,8 @@ int pccp_propagate_ex(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_
   a.team_size = plan.team;
   a.teams = plan.teams;
   a.max_iter = (cfg && cfg->max_iterations > 0) ? cfg->max_iterations : m->max_iter;
-  a.linear_mode = (cfg && cfg->linear_mode > 0) ? cfg->linear_mode - 1 : kDefaultLinearMode;
+  a.track_words = track_words(m->n_vars, m->n_lin);
+  a.work = work;
   plan.kern<<<plan.grid, plan.team * plan.teams, plan.smem, s>>>(a);
   const cudaError_t le = cudaGetLastError();
   cudaFreeAsync(counter, s);
@@ -637,7 +739,7 @@ int pccp_propagate_ex(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_
 
 int pccp_propagate(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_t* ub,
                    int32_t* status, int32_t* iterations, void* stream) {
-  return pccp_propagate_ex(m, n_stores, lb, ub, status, iterations, nullptr, stream);
+  return pccp_propagate_ex(m, n_stores, lb, ub, status, iterations, nullptr, nullptr, stream);
 }
 
 int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
@@ -655,7 +757,7 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
 
   std::vector<InstanceDesc> desc(n_models);
   uint32_t max_img = 0;
-  int32_t max_vars = 0, max_branch = 0;
+  int32_t max_vars = 0, max_branch = 0, max_tw = 0;
   int64_t wit_total = 0;
   for (int32_t i = 0; i < n_models; ++i) {
     const pccp_model* m = models[i];
@@ -674,14 +776,15 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     max_img = std::max(max_img, m->image_bytes);
     max_vars = std::max(max_vars, m->n_vars);
     max_branch = std::max(max_branch, m->n_branch);
+    max_tw = std::max(max_tw, track_words(m->n_vars, m->n_lin));
   }
-  const size_t smem = static_cast<size_t>(max_img) + 16 + sizeof(SearchCtrl) +
-                      static_cast<size_t>(max_vars) * sizeof(int2);
+  const size_t smem = solve_smem(max_img, max_tw, max_vars);
   if (smem > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
-  PCCP_CUDA(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const auto ksolve = opts->skip_stable ? k_solve<true> : k_solve<false>;
+  PCCP_CUDA(cudaFuncSetAttribute(ksolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
   int per_sm = 0;
-  PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, threads, smem));
+  PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksolve, threads, smem));
   if (per_sm < 1) return PCCP_ERR_SMEM;
   int grid = std::min(n_models, sms * per_sm);
   if (opts->blocks > 0) grid = std::min(grid, static_cast<int>(opts->blocks));
@@ -723,16 +826,16 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     a.mode = opts->mode;
     a.strategy = opts->strategy;
     a.obj_ub = opts->obj_ub;
-    a.linear_mode = kDefaultLinearMode;
     a.node_limit = opts->node_limit;
     a.time_limit_ns = opts->time_limit_ms > 0 ? opts->time_limit_ms * 1000000ll : 0;
     a.max_image_bytes = max_img;
+    a.max_track_words = max_tw;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
       rc = PCCP_ERR_CUDA;
       break;
     }
     cudaEventRecord(e0, s);
-    k_solve<<<grid, threads, smem, s>>>(a);
+    ksolve<<<grid, threads, smem, s>>>(a);
     if (cudaGetLastError() != cudaSuccess) {
       rc = PCCP_ERR_CUDA;
       break;
@@ -767,7 +870,7 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     o.solutions = r.solutions;
     o.iterations = r.iterations;
     const pccp_model* m = models[i];
-    o.rows_evaluated = r.iterations * static_cast<int64_t>(m->n_t + m->n_rf + m->n_lin);
+    o.rows_evaluated = r.evals;
     o.max_depth = r.max_depth;
     o.elapsed_ms = ms;
     if (o.witness && r.has_solution)
@@ -793,18 +896,21 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   const int team = o->threads > 0 ? o->threads : 128;
   if (team % 32 != 0 || team > 1024) return PCCP_ERR_INVALID;
   const size_t base = static_cast<size_t>(m->image_bytes) + 16;
-  const size_t per_team = sizeof(EpsCtrl) + static_cast<size_t>(m->n_vars) * sizeof(int2);
+  const size_t per_team = sizeof(EpsCtrl) + 4 * ((track_words(m->n_vars, m->n_lin) + 3) & ~3) +
+                          static_cast<size_t>(m->n_vars) * sizeof(int2);
   if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   const int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
   const int teams = std::max(1, std::min({8, fit, 1024 / team}));
   const size_t smem = base + static_cast<size_t>(teams) * per_team;
-  PCCP_CUDA(cudaFuncSetAttribute(k_eps_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const auto kexp = o->skip_stable ? k_eps_expand<true> : k_eps_expand<false>;
+  const auto ksol = o->skip_stable ? k_eps_solve<true> : k_eps_solve<false>;
+  PCCP_CUDA(cudaFuncSetAttribute(kexp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
-  PCCP_CUDA(cudaFuncSetAttribute(k_eps_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PCCP_CUDA(cudaFuncSetAttribute(ksol, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
   int occ_e = 0, occ_s = 0;
-  PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_e, k_eps_expand, teams * team, smem));
-  PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_eps_solve, teams * team, smem));
+  PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_e, kexp, teams * team, smem));
+  PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, ksol, teams * team, smem));
   const int per_sm = std::min(occ_e, occ_s);
   if (per_sm < 1) return PCCP_ERR_SMEM;
   int grid = sms * per_sm;
@@ -862,7 +968,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     a.mode = o->mode;
     a.strategy = o->strategy;
     a.obj_ub = o->obj_ub;
-    a.linear_mode = kDefaultLinearMode;
+    a.track_words = track_words(m->n_vars, m->n_lin);
     a.node_limit = o->node_limit;
     a.time_limit_ns = o->time_limit_ms > 0 ? o->time_limit_ms * 1000000ll : 0;
     uint8_t* lin = d + o_la;
@@ -881,7 +987,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
         rc = PCCP_ERR_CUDA;
         break;
       }
-      k_eps_expand<<<grid, teams * team, smem, s>>>(a);
+      kexp<<<grid, teams * team, smem, s>>>(a);
       if (cudaGetLastError() != cudaSuccess) {
         rc = PCCP_ERR_CUDA;
         break;
@@ -916,7 +1022,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
         rc = PCCP_ERR_CUDA;
         break;
       }
-      k_eps_solve<<<grid, teams * team, smem, s>>>(a);
+      ksol<<<grid, teams * team, smem, s>>>(a);
       if (cudaGetLastError() != cudaSuccess) {
         rc = PCCP_ERR_CUDA;
         break;
@@ -947,7 +1053,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     res->fails = static_cast<int64_t>(hg.fails);
     res->solutions = static_cast<int64_t>(hg.solutions);
     res->iterations = static_cast<int64_t>(hg.iterations);
-    res->rows_evaluated = res->iterations * static_cast<int64_t>(m->n_t + m->n_rf + m->n_lin);
+    res->rows_evaluated = static_cast<int64_t>(hg.evals);
     res->max_depth = hg.max_depth;
     res->elapsed_ms = ms;
     res->status = hg.limited ? PCCP_RES_LIMIT
@@ -995,3 +1101,4 @@ int pccp_solve(const pccp_model* m, const pccp_solve_opts* opts, pccp_result* re
 }  // extern "C"
 
 #include "pccp_noalloc.inc"
+#include "pccp_batch.inc"

@@ -24,22 +24,34 @@ enum : int { kFixpoint = 0, kFailed = 1, kError = 2 };
 // and 16-byte aligned.
 struct TableHeader {
   int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective, image_bytes;
-  int32_t off_t, off_rf, off_lin, off_terms, off_branch, pad0, pad1, pad2;
+  int32_t off_t, off_rf, off_lin, off_terms, off_branch, n_lin_long, off_lin_long, off_terms_long;
+  int32_t off_adj_off, off_adj, n_adj, pad[5];
 };
-static_assert(sizeof(TableHeader) == 64, "header must be 64 bytes");
+static_assert(sizeof(TableHeader) == 96, "header must be 96 bytes");
 
 // Row encodings (structure of arrays, one array per row kind):
 //   temporal  uint2 {x | y << 16, d}              x + d <= y
 //   reified   uint2 {x | y << 16, b | d << 16}    b <=> (x <= y && y < x + d), d int16
-//   linear    int4  {c, first term, len, 0}       sum coef*var <= c
+//   linear    int4  {c, base, len, 0}             sum coef*var <= c
 //   term      uint32 var | coef << 16             coef int16
+// Linear rows of at most kShortRow terms are evaluated by one thread each and
+// stored in tiles of 32 rows, transposed: term t of the row in lane l of a
+// tile sits at base + 32 t, base = tile start + l, so the 32 lanes of a warp
+// read 32 consecutive words.  Longer rows are evaluated by a warp each and
+// stored row-major (term k at base + k).
+constexpr int kShortRow = 64;
+
 struct Tab {
   const uint2* t;
   const uint2* rf;
-  const int4* lin;
-  const uint32_t* terms;
+  const int4* lin;          // short rows
+  const uint32_t* terms;    // their tiled terms
+  const int4* lin_long;     // long rows
+  const uint32_t* terms_long;
   const int32_t* branch;
-  int n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective;
+  const int32_t* adj_off;   // [n_vars + 1]: linear rows holding each variable
+  const int32_t* adj;       // row ids: short rows 0.., long rows n_lin..
+  int n_vars, n_t, n_rf, n_lin, n_lin_long, n_terms, n_branch, objective;
 };
 
 __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
@@ -56,7 +68,12 @@ __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
   tb.rf = reinterpret_cast<const uint2*>(img + h->off_rf);
   tb.lin = reinterpret_cast<const int4*>(img + h->off_lin);
   tb.terms = reinterpret_cast<const uint32_t*>(img + h->off_terms);
+  tb.n_lin_long = h->n_lin_long;
+  tb.lin_long = reinterpret_cast<const int4*>(img + h->off_lin_long);
+  tb.terms_long = reinterpret_cast<const uint32_t*>(img + h->off_terms_long);
   tb.branch = reinterpret_cast<const int32_t*>(img + h->off_branch);
+  tb.adj_off = reinterpret_cast<const int32_t*>(img + h->off_adj_off);
+  tb.adj = reinterpret_cast<const int32_t*>(img + h->off_adj);
   return tb;
 }
 
@@ -137,7 +154,57 @@ struct Team {
 struct Flags {
   bool ch;  // some tell strengthened the store
   bool fl;  // some tell found an empty interval
+  int evals;  // rows evaluated by this thread
+  int bytes;  // algorithmic bytes read by this thread (rows, bounds, checks)
 };
+
+// Change tracking of one team (shared memory).  Three rotating pairs of
+// bitmaps (the past / present / future rotation of the has_changed flags of
+// Sec. 5): chg marks variables strengthened during an iteration, dl marks
+// the linear rows holding such a variable.  Iteration k writes buffer k%3,
+// reads buffer (k+2)%3 (the previous iteration's changes) and clears
+// buffer (k+1)%3 for the next iteration.  A row whose variables did not
+// change since its last evaluation is stable and is skipped: the fixed point
+// is unchanged because every row that could still tell something is run
+// again after each change of its inputs (the fair-schedule argument of
+// Sec. 3).
+struct Track {
+  uint32_t* chg;  // [3][W]
+  uint32_t* dl;   // [3][WL]
+  int W, WL;
+};
+
+__host__ __device__ __forceinline__ int track_words(int n_vars, int n_lin_rows) {
+  return 3 * ((n_vars + 31) / 32) + 3 * ((n_lin_rows + 31) / 32);
+}
+
+__device__ __forceinline__ Track make_track(uint32_t* base, int n_vars, int n_lin_rows) {
+  Track t;
+  t.W = (n_vars + 31) / 32;
+  t.WL = (n_lin_rows + 31) / 32;
+  t.chg = base;
+  t.dl = base + 3 * t.W;
+  return t;
+}
+
+__device__ __forceinline__ void atom_or_u32(uint32_t* p, uint32_t v) {
+  asm volatile("atom.relaxed.cta.shared::cta.or.b32 _, [%0], %1;" ::"r"(smem_u32(p)), "r"(v)
+               : "memory");
+}
+
+__device__ __forceinline__ bool test_bit(const uint32_t* bm, int i) {
+  return (bm[i >> 5] >> (i & 31)) & 1u;
+}
+
+// Record that variable v changed in buffer `cur`: its bit, and the dirty
+// bits of the linear rows that hold it.
+__device__ __forceinline__ void mark_changed(const Tab& tb, const Track& tk, int cur, int v) {
+  atom_or_u32(&tk.chg[cur * tk.W + (v >> 5)], 1u << (v & 31));
+  for (int k = tb.adj_off[v]; k < tb.adj_off[v + 1]; ++k) {
+    const int r = tb.adj[k];
+    atom_or_u32(&tk.dl[cur * tk.WL + (r >> 5)], 1u << (r & 31));
+  }
+}
 
 // floor(a / b) for b > 0.
 __device__ __forceinline__ int floor_div_pos(int a, int b) {
@@ -149,38 +216,66 @@ __device__ __forceinline__ int floor_div_pos(int a, int b) {
 // Join cand into lb(v).  lb_seen/ub_seen are the values this thread loaded;
 // bounds only move inward, so cand <= lb_seen means the tell is a no-op and
 // cand > ub_seen means the interval is empty whatever happened since.
-__device__ __forceinline__ void tell_lb(int2* st, int v, int cand, int lb_seen, int ub_seen,
+// Context of one sweep: the table, the store, the change tracking, the
+// buffer written this iteration and the one read (the previous iteration's
+// changes), and whether every row must run (first iteration of a fresh store).
+struct Sweep {
+  const Tab& tb;
+  int2* st;
+  const Track& tk;
+  int cur;
+  const uint32_t* prev_chg;
+  const uint32_t* prev_dl;
+  bool full;
+};
+
+template <bool kTrack>
+__device__ __forceinline__ void tell_lb(const Sweep& w, int v, int cand, int lb_seen, int ub_seen,
                                         Flags& f) {
   if (cand <= lb_seen) return;
   if (cand > ub_seen) {
     f.fl = true;
     return;
   }
-  int old = atom_max_s32(&st[v].x, cand);
-  if (old < cand) f.ch = true;
+  int old = atom_max_s32(&w.st[v].x, cand);
+  if (old < cand) {
+    f.ch = true;
+    if (kTrack) mark_changed(w.tb, w.tk, w.cur, v);
+  }
 }
 
-__device__ __forceinline__ void tell_ub(int2* st, int v, int cand, int lb_seen, int ub_seen,
+template <bool kTrack>
+__device__ __forceinline__ void tell_ub(const Sweep& w, int v, int cand, int lb_seen, int ub_seen,
                                         Flags& f) {
   if (cand >= ub_seen) return;
   if (cand < lb_seen) {
     f.fl = true;
     return;
   }
-  int old = atom_min_s32(&st[v].y, cand);
-  if (old > cand) f.ch = true;
+  int old = atom_min_s32(&w.st[v].y, cand);
+  if (old > cand) {
+    f.ch = true;
+    if (kTrack) mark_changed(w.tb, w.tk, w.cur, v);
+  }
 }
 
 // Temporal row x + d <= y: ub(x) <= ub(y) - d and lb(y) >= lb(x) + d
 // (the [[x + y <= c]] compilation of Sec. 2 with y negated).  The common case
 // (nothing to tell) costs one branch.
-__device__ __forceinline__ void eval_temporal(uint2 row, int2* st, Flags& f) {
+template <bool kTrack>
+__device__ __forceinline__ void eval_temporal(const Sweep& w, uint2 row, Flags& f) {
   const int x = row.x & 0xffff, y = row.x >> 16, d = static_cast<int>(row.y);
-  const int2 X = ld_dom(st, x), Y = ld_dom(st, y);
+  if (kTrack && !w.full && !(test_bit(w.prev_chg, x) | test_bit(w.prev_chg, y))) {
+    f.bytes += 16;  // row and two change words
+    return;
+  }
+  f.evals += 1;
+  f.bytes += 20;
+  const int2 X = ld_dom(w.st, x), Y = ld_dom(w.st, y);
   const int cux = Y.y - d, cly = X.x + d;
   if (cux < X.y || cly > Y.x) {
-    tell_ub(st, x, cux, X.x, X.y, f);
-    tell_lb(st, y, cly, Y.x, Y.y, f);
+    tell_ub<kTrack>(w, x, cux, X.x, X.y, f);
+    tell_lb<kTrack>(w, y, cly, Y.x, Y.y, f);
   }
 }
 
@@ -188,10 +283,18 @@ __device__ __forceinline__ void eval_temporal(uint2 row, int2* st, Flags& f) {
 // [[phi <=> psi]] (Sec. 2) evaluated on one snapshot; the candidates of every
 // ask are joined per bound with selects, and the tells (rare once the store
 // settles) sit behind one branch.
-__device__ __forceinline__ void eval_reified(uint2 row, int2* st, Flags& f) {
+template <bool kTrack>
+__device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f) {
   const int x = row.x & 0xffff, y = row.x >> 16;
   const int b = row.y & 0xffff, d = static_cast<int>(row.y) >> 16;
-  const int2 X = ld_dom(st, x), Y = ld_dom(st, y), B = ld_dom(st, b);
+  if (kTrack && !w.full &&
+      !(test_bit(w.prev_chg, x) | test_bit(w.prev_chg, y) | test_bit(w.prev_chg, b))) {
+    f.bytes += 20;  // row and three change words
+    return;
+  }
+  f.evals += 1;
+  f.bytes += 40;
+  const int2 X = ld_dom(w.st, x), Y = ld_dom(w.st, y), B = ld_dom(w.st, b);
   const bool entA = X.y <= Y.x;           // ub x <= lb y
   const bool entB = Y.y <= X.x + d - 1;   // ub y <= lb x + d - 1
   const bool entNA = X.x >= Y.y + 1;      // lb x >= ub y + 1
@@ -217,30 +320,40 @@ __device__ __forceinline__ void eval_reified(uint2 row, int2* st, Flags& f) {
   const int nlb = (entA && entB) ? max(B.x, 1) : B.x;    // A and B entailed: b
   const int nub = (entNA || entNB) ? min(B.y, 0) : B.y;  // not (A and B) entailed: not b
   if (nlx > X.x || nux < X.y || nly > Y.x || nuy < Y.y || nlb > B.x || nub < B.y) {
-    tell_lb(st, x, nlx, X.x, X.y, f);
-    tell_ub(st, x, nux, X.x, X.y, f);
-    tell_lb(st, y, nly, Y.x, Y.y, f);
-    tell_ub(st, y, nuy, Y.x, Y.y, f);
-    tell_lb(st, b, nlb, B.x, B.y, f);
-    tell_ub(st, b, nub, B.x, B.y, f);
+    tell_lb<kTrack>(w, x, nlx, X.x, X.y, f);
+    tell_ub<kTrack>(w, x, nux, X.x, X.y, f);
+    tell_lb<kTrack>(w, y, nly, Y.x, Y.y, f);
+    tell_ub<kTrack>(w, y, nuy, Y.x, Y.y, f);
+    tell_lb<kTrack>(w, b, nlb, B.x, B.y, f);
+    tell_ub<kTrack>(w, b, nub, B.x, B.y, f);
   }
 }
 
-// Linear row sum a_k x_k <= c, one warp per row, lanes over terms.  S is the
+// Long linear row sum a_k x_k <= c, one warp per row, lanes over terms.  S is the
 // minimum of the whole sum over the box; term k may be bounded by
 // slack_k = c - (S - min_k).  If S + (largest span of one term) <= c no term
 // can move, so the second pass is skipped.  Terms of the first 32 stay in
 // registers; longer rows reload theirs (a fresher bound only weakens the
 // tell, which stays sound, and the last iteration sees a stable store).
-__device__ __forceinline__ void eval_linear_warp(const Tab& tb, int r, int lane, int2* st,
-                                                 Flags& f) {
-  const int4 h = tb.lin[r];
+template <bool kTrack>
+__device__ __forceinline__ void eval_linear_warp(const Sweep& w, int r, int lane, Flags& f) {
+  const Tab& tb = w.tb;
+  int2* st = w.st;
+  if (kTrack && !w.full && !test_bit(w.prev_dl, tb.n_lin + r)) {
+    if (lane == 0) f.bytes += 4;
+    return;
+  }
+  const int4 h = tb.lin_long[r];
+  if (lane == 0) {
+    f.evals += 1;
+    f.bytes += 12 + 12 * h.z;
+  }
   const int c = h.x, off = h.y, len = h.z;
   int S = 0, span = 0;
   int v0 = 0, a0 = 0;
   int2 D0 = make_int2(0, 0);
   for (int k = lane; k < len; k += 32) {
-    const uint32_t t = tb.terms[off + k];
+    const uint32_t t = tb.terms_long[off + k];
     const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
     const int2 D = ld_dom(st, v);
     const int mt = a > 0 ? a * D.x : a * D.y;
@@ -268,7 +381,7 @@ __device__ __forceinline__ void eval_linear_warp(const Tab& tb, int r, int lane,
       a = a0;
       D = D0;
     } else {
-      const uint32_t t = tb.terms[off + k];
+      const uint32_t t = tb.terms_long[off + k];
       v = t & 0xffff;
       a = static_cast<int>(t) >> 16;
       D = ld_dom(st, v);
@@ -276,24 +389,33 @@ __device__ __forceinline__ void eval_linear_warp(const Tab& tb, int r, int lane,
     const int mt = a > 0 ? a * D.x : a * D.y;
     const int slack = c - (S - mt);
     if (a > 0) {
-      if (a * D.y > slack) tell_ub(st, v, floor_div_pos(slack, a), D.x, D.y, f);
+      if (a * D.y > slack) tell_ub<kTrack>(w, v, floor_div_pos(slack, a), D.x, D.y, f);
     } else {
       // a x <= slack with a < 0: x >= ceil(slack / a) = -floor(slack / -a)
-      if (a * D.x > slack) tell_lb(st, v, -floor_div_pos(slack, -a), D.x, D.y, f);
+      if (a * D.x > slack) tell_lb<kTrack>(w, v, -floor_div_pos(slack, -a), D.x, D.y, f);
     }
   }
 }
 
-// Linear row sum a_k x_k <= c evaluated by one thread: the same two passes
-// as eval_linear_warp with the sum kept in a register (no warp reduction and
-// no idle lanes on rows shorter than a warp).
-__device__ __forceinline__ void eval_linear_thread(const Tab& tb, int r, int2* st, Flags& f) {
+// Short linear row sum a_k x_k <= c evaluated by one thread: the same two
+// passes as eval_linear_warp with the sum kept in a register (no warp
+// reduction and no idle lanes on rows shorter than a warp).
+template <bool kTrack>
+__device__ __forceinline__ void eval_linear_thread(const Sweep& w, int r, Flags& f) {
+  const Tab& tb = w.tb;
+  int2* st = w.st;
+  if (kTrack && !w.full && !test_bit(w.prev_dl, r)) {
+    f.bytes += 4;
+    return;
+  }
   const int4 h = tb.lin[r];
-  const int c = h.x, off = h.y, len = h.z;
+  const int c = h.x, base = h.y, len = h.z;
+  f.evals += 1;
+  f.bytes += 12 + 12 * len;
   int S = 0, span = 0;
 #pragma unroll 4
   for (int k = 0; k < len; ++k) {
-    const uint32_t t = tb.terms[off + k];
+    const uint32_t t = tb.terms[base + 32 * k];
     const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
     const int2 D = ld_dom(st, v);
     S += a > 0 ? a * D.x : a * D.y;
@@ -305,51 +427,83 @@ __device__ __forceinline__ void eval_linear_thread(const Tab& tb, int r, int2* s
   }
   if (S + span <= c) return;
   for (int k = 0; k < len; ++k) {
-    const uint32_t t = tb.terms[off + k];
+    const uint32_t t = tb.terms[base + 32 * k];
     const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
     const int2 D = ld_dom(st, v);
     const int mt = a > 0 ? a * D.x : a * D.y;
     const int slack = c - (S - mt);
     if (a > 0) {
-      if (a * D.y > slack) tell_ub(st, v, floor_div_pos(slack, a), D.x, D.y, f);
+      if (a * D.y > slack) tell_ub<kTrack>(w, v, floor_div_pos(slack, a), D.x, D.y, f);
     } else {
-      if (a * D.x > slack) tell_lb(st, v, -floor_div_pos(slack, -a), D.x, D.y, f);
+      if (a * D.x > slack) tell_lb<kTrack>(w, v, -floor_div_pos(slack, -a), D.x, D.y, f);
     }
   }
 }
 
 // One full evaluation of every row of the table (one iteration of the
-// eventless loop).  Rows of one kind run back to back so warps stay uniform.
-// linear_mode 0: a warp per linear row; 1: a thread per linear row.
-__device__ __forceinline__ void sweep_rows(const Tab& tb, int2* st, const Team& tm, Flags& f,
-                                           int linear_mode) {
-  for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified(tb.rf[r], st, f);
-  for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal(tb.t[r], st, f);
-  if (linear_mode == 1) {
-    for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) eval_linear_thread(tb, r, st, f);
-  } else {
-    for (int r = tm.warp; r < tb.n_lin; r += tm.nwarps) eval_linear_warp(tb, r, tm.lane, st, f);
-  }
+// eventless loop).  Rows of one kind run back to back so warps stay uniform:
+// a thread per reified, temporal and short linear row, a warp per long
+// linear row.
+template <bool kTrack>
+__device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags& f) {
+  const Tab& tb = w.tb;
+  for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack>(w, tb.rf[r], f);
+  for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
+  for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) eval_linear_thread<kTrack>(w, r, f);
+  for (int r = tm.warp; r < tb.n_lin_long; r += tm.nwarps)
+    eval_linear_warp<kTrack>(w, r, tm.lane, f);
 }
+
+// Per-team scalars of the fixed point (shared memory): failure flag and the
+// work counters of the current store.
+struct FixCtrl {
+  int fail;
+  int evals;
+  int bytes;
+  int pad;
+};
 
 // Fixed-point loop of one team on its store `st` (Sec. 5): iterate until an
 // iteration changes nothing or some tell finds an empty interval.  Failure is
 // checked inside the loop (an infeasible cycle would otherwise keep raising
 // bounds); when the loop goes quiet a final scan catches an interval emptied
 // by two concurrent tells that each saw a stale opposite bound.
-// Preconditions: st staged and published to the team by a barrier; *fail == 0
-// and published.  The caller must not modify *fail before the next team
-// barrier after this returns.  Team-uniform return value.
-__device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team& tm, int* fail,
-                                             int max_iter, int& iters, int linear_mode) {
+// kTrack = false: the eventless loop of Sec. 5 (every row every iteration).
+// kTrack = true: stable rows are skipped.  With full = true every row runs
+// in the first iteration (a store nothing is known about); with full = false
+// only the rows marked in change buffer 2 do (a fixed point strengthened by a
+// few tells, each marked by the caller with mark_changed(.., 2, v)).  Later
+// iterations run the rows whose inputs changed in the iteration before.
+// Preconditions (published to the team by a barrier): st staged; change
+// buffer 0 cleared; buffer 2 cleared except for the caller's marks when
+// full = false; fc->fail, evals, bytes == 0.  The caller must not modify *fc
+// or the change buffers before the next team barrier after this returns.
+// Team-uniform return value; fc->evals / fc->bytes are valid after return.
+template <bool kTrack>
+__device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team& tm, FixCtrl* fc,
+                                             const Track& tk, bool full, int max_iter,
+                                             int& iters) {
   int it = 0;
   for (;;) {
-    Flags f{false, false};
-    sweep_rows(tb, st, tm, f, linear_mode);
-    if (f.fl) st_relaxed(fail, 1);
+    const int cur = it % 3, prv = (it + 2) % 3, nxt = (it + 1) % 3;
+    if (kTrack) {
+      for (int i = tm.tid; i < tk.W; i += tm.nthr) tk.chg[nxt * tk.W + i] = 0u;
+      for (int i = tm.tid; i < tk.WL; i += tm.nthr) tk.dl[nxt * tk.WL + i] = 0u;
+    }
+    const Sweep w{tb, st, tk, cur, tk.chg + prv * tk.W, tk.dl + prv * tk.WL, full || !kTrack};
+    Flags f{false, false, 0, 0};
+    sweep_rows<kTrack>(w, tm, f);
+    const int ev = __reduce_add_sync(0xffffffffu, f.evals);
+    const int by = __reduce_add_sync(0xffffffffu, f.bytes);
+    if (tm.lane == 0) {
+      atomicAdd(&fc->evals, ev);
+      atomicAdd(&fc->bytes, by);
+    }
+    if (f.fl) st_relaxed(&fc->fail, 1);
     ++it;
+    full = false;
     const bool any = team_bar_or(tm.bar, tm.nthr, f.ch || f.fl);
-    if (ld_relaxed(fail)) {
+    if (ld_relaxed(&fc->fail)) {
       iters = it;
       return kFailed;
     }
@@ -366,6 +520,18 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
   }
   iters = it;
   return team_bar_or(tm.bar, tm.nthr, empty) ? kFailed : kFixpoint;
+}
+
+// Clear change buffers 0 and 2 (before a fixed point); team threads, strided.
+__device__ __forceinline__ void track_clear02(const Track& tk, const Team& tm) {
+  for (int i = tm.tid; i < tk.W; i += tm.nthr) {
+    tk.chg[i] = 0u;
+    tk.chg[2 * tk.W + i] = 0u;
+  }
+  for (int i = tm.tid; i < tk.WL; i += tm.nthr) {
+    tk.dl[i] = 0u;
+    tk.dl[2 * tk.WL + i] = 0u;
+  }
 }
 
 // ------------------------------------------------ bulk copy of the table image

@@ -39,11 +39,14 @@ def generic_batch(seed, n_stores, **kw):
 
 CONFIGS = [None,
            pccp.launch_config(32, 1),
-           pccp.launch_config(64, 4, linear_mode=1),
-           pccp.launch_config(64, 4, linear_mode=2),
-           pccp.launch_config(256, 2, linear_mode=1),
-           pccp.launch_config(1024, 1, linear_mode=2),
-           pccp.launch_config(96, 10, 1)]
+           pccp.launch_config(64, 4),
+           pccp.launch_config(128, 8),
+           pccp.launch_config(256, 2),
+           pccp.launch_config(1024, 1),
+           pccp.launch_config(96, 10, 1),
+           pccp.launch_config(128, 4, skip_stable=True),
+           pccp.launch_config(64, 8, skip_stable=True),
+           pccp.launch_config(1024, 1, skip_stable=True)]
 
 
 @pytest.mark.parametrize("cfg_i", range(len(CONFIGS)))
@@ -85,6 +88,17 @@ def test_j30_nodes_bit_exact():
     x, f = compare_batch(om, lb, ub, st, glb, gub)
     assert x > 100 and f > 100
     assert (it[st == 0] >= 1).all()
+    # work report: every row runs in the first iteration, stable rows are
+    # skipped afterwards, never more than iterations x rows
+    dlb = torch.from_numpy(lb).cuda()
+    dub = torch.from_numpy(ub).cuda()
+    work = torch.zeros((len(nodes), 2), dtype=torch.int32, device="cuda")
+    st2, it2 = pccp.propagate(m, dlb, dub, work=work, config=pccp.launch_config(skip_stable=True))
+    torch.cuda.synchronize()
+    w, it2 = work.cpu().numpy(), it2.cpu().numpy()
+    ok = st2.cpu().numpy() == 0
+    assert (w[ok, 0] >= m.rows).all() and (w[ok, 0] <= it2[ok] * m.rows).all()
+    assert w[ok, 0].sum() < it2[ok].sum() * m.rows  # something was skipped
 
 
 def test_uneven_models_bit_exact():

@@ -150,3 +150,34 @@ def test_parallel_node_limited_j30():
     d = oracle.solve(rcpsp_model(inst), node_limit=2_000)  # the parallel search does better
     if d["has_solution"]:
         assert r["objective"] <= d["objective"]
+
+
+
+# ------------------------------- skipping stable rows keeps every result exact
+
+def test_skip_stable_search_is_exact():
+    for seed in range(0, 100, 6):
+        inst = config_instance("tiny8", seed)
+        m, om = pccp.Model.from_rcpsp(inst), rcpsp_model(inst)
+        same(pccp.solve(m, skip_stable=True), oracle.solve(om))
+        same(pccp.solve(m, strategy=pccp.PCCP_FIRST_FAIL, skip_stable=True),
+             oracle.solve(om, strategy=oracle.FIRST_FAIL))
+    insts = [config_instance("mixed30_60", s) for s in range(8)]
+    res = pccp.solve_batch([pccp.Model.from_rcpsp(i) for i in insts], node_limit=300,
+                           skip_stable=True)
+    for inst, r in zip(insts, res):
+        same(r, oracle.solve(rcpsp_model(inst), node_limit=300))
+
+
+def test_skip_stable_parallel_counts_are_exact():
+    for seed in range(0, 100, 13):
+        inst = config_instance("tiny8", seed)
+        m, om = pccp.Model.from_rcpsp(inst), rcpsp_model(inst)
+        opt = oracle.solve(om)["objective"]
+        c = oracle.solve(om, mode=oracle.COUNT_ALL, obj_ub=opt)
+        r = pccp.solve(m, mode=pccp.PCCP_COUNT_ALL, obj_ub=opt, deterministic=False,
+                       skip_stable=True)
+        assert (r["nodes"], r["fails"], r["solutions"]) == (c["nodes"], c["fails"], c["solutions"])
+        r2 = pccp.solve(m, deterministic=False, skip_stable=True)
+        assert r2["objective"] == opt
+        _check_rcpsp_witness(inst, r2)

@@ -44,7 +44,7 @@ def test_noalloc_matches_batch_on_two_calls_in_a_row():
 
 def test_noalloc_rejects_requests_beyond_its_scratch():
     m = pccp.Model.from_rcpsp(config_instance("tiny8", 0))
-    per_model = 40 + 56 + 4 * m.n_vars
+    per_model = 40 + 64 + 4 * m.n_vars
     n = (8 << 20) // per_model + 16
     with pytest.raises(pccp.PccpError) as e:
         pccp.solve_batch([m] * n, noalloc=True)
