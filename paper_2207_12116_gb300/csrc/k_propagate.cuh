@@ -26,6 +26,7 @@ struct PropArgs {
   int teams;
   int max_iter;
   int track_words;
+  int table_global;  // 1: rows are read from the device image (too big for shared memory)
 };
 
 // Per-team scalars of k_propagate (shared memory).
@@ -40,16 +41,22 @@ struct PropCtrl {
 template <int kMaxThreads, int kMinBlocks, bool kTrack>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
+  // shared memory: [table image, unless it is read from global memory]
+  //                [mbarrier 16 B][PropCtrl x teams][change words x teams][stores]
+  const size_t img_bytes = a.table_global ? 0 : a.image_bytes;
   uint8_t* img = smem;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + a.image_bytes);
-  PropCtrl* ctrl_base = reinterpret_cast<PropCtrl*>(smem + a.image_bytes + 16);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + img_bytes);
+  PropCtrl* ctrl_base = reinterpret_cast<PropCtrl*>(smem + img_bytes + 16);
   const int tw16 = (a.track_words + 3) & ~3;  // words, 16-byte multiple
   uint32_t* track_base =
-      reinterpret_cast<uint32_t*>(smem + a.image_bytes + 16 + sizeof(PropCtrl) * a.teams);
+      reinterpret_cast<uint32_t*>(smem + img_bytes + 16 + sizeof(PropCtrl) * a.teams);
   int2* st_base = reinterpret_cast<int2*>(track_base + static_cast<size_t>(tw16) * a.teams);
 
-  if (threadIdx.x == 0) mbar_init(mbar, 1);
-  const bool ok = load_image(img, a.image, a.image_bytes, mbar, 0);
+  bool ok = true;
+  if (!a.table_global) {
+    if (threadIdx.x == 0) mbar_init(mbar, 1);
+    ok = load_image(img, a.image, a.image_bytes, mbar, 0);
+  }
 
   const int team_id = threadIdx.x / a.team_size;
   Team tm;
@@ -61,7 +68,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   tm.nwarps = a.team_size >> 5;
   PropCtrl* ctrl = ctrl_base + team_id;
   int2* st = st_base + static_cast<size_t>(team_id) * a.n_vars;
-  const Tab tb = make_tab(img);
+  const Tab tb = make_tab(a.table_global ? a.image : img);
   const Track tk = make_track(track_base + static_cast<size_t>(tw16) * team_id, tb.n_vars,
                               tb.n_lin + tb.n_lin_long);
   const int nv = a.n_vars;

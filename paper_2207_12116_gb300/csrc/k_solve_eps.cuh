@@ -53,6 +53,7 @@ struct EpsArgs {
   int strategy;
   int obj_ub;
   int track_words;
+  int table_global;  // 1: rows are read from the device image
   int64_t node_limit;
   int64_t time_limit_ns;
 };
@@ -216,13 +217,14 @@ struct EpsSmem {
 
 __device__ __forceinline__ EpsSmem eps_smem(uint8_t* smem, const EpsArgs& a, int team_id) {
   EpsSmem s;
+  const size_t img_bytes = a.table_global ? 0 : a.image_bytes;
   s.img = smem;
-  s.mbar = reinterpret_cast<uint64_t*>(smem + a.image_bytes);
-  EpsCtrl* ctrl = reinterpret_cast<EpsCtrl*>(smem + a.image_bytes + 16);
+  s.mbar = reinterpret_cast<uint64_t*>(smem + img_bytes);
+  EpsCtrl* ctrl = reinterpret_cast<EpsCtrl*>(smem + img_bytes + 16);
   s.sc = ctrl + team_id;
   const int tw16 = (a.track_words + 3) & ~3;
   uint32_t* track_base =
-      reinterpret_cast<uint32_t*>(smem + a.image_bytes + 16 + sizeof(EpsCtrl) * a.teams);
+      reinterpret_cast<uint32_t*>(smem + img_bytes + 16 + sizeof(EpsCtrl) * a.teams);
   s.track = track_base + static_cast<size_t>(tw16) * team_id;
   int2* st_base = reinterpret_cast<int2*>(track_base + static_cast<size_t>(tw16) * a.teams);
   s.st = st_base + static_cast<size_t>(team_id) * a.n_vars;
@@ -248,15 +250,17 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
   const EpsSmem sm = eps_smem(smem, a, team_id);
-  if (threadIdx.x == 0) mbar_init(sm.mbar, 1);
-  if (!load_image(sm.img, a.image, a.image_bytes, sm.mbar, 0)) {
-    if (threadIdx.x == 0) atomicExch(&a.g->error, 3);
-    return;
+  if (!a.table_global) {
+    if (threadIdx.x == 0) mbar_init(sm.mbar, 1);
+    if (!load_image(sm.img, a.image, a.image_bytes, sm.mbar, 0)) {
+      if (threadIdx.x == 0) atomicExch(&a.g->error, 3);
+      return;
+    }
   }
   if (threadIdx.x == 0 && blockIdx.x == 0 && a.g->t0 == 0)
     atomicCAS(&a.g->t0, 0ull, static_cast<unsigned long long>(eps_now_ns()));
   const Team tm = eps_team(a, team_id);
-  const Tab tb = make_tab(sm.img);
+  const Tab tb = make_tab(a.table_global ? a.image : sm.img);
   const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
   EpsCtrl* sc = sm.sc;
@@ -336,15 +340,17 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
   const EpsSmem sm = eps_smem(smem, a, team_id);
-  if (threadIdx.x == 0) mbar_init(sm.mbar, 1);
-  if (!load_image(sm.img, a.image, a.image_bytes, sm.mbar, 0)) {
-    if (threadIdx.x == 0) atomicExch(&a.g->error, 3);
-    return;
+  if (!a.table_global) {
+    if (threadIdx.x == 0) mbar_init(sm.mbar, 1);
+    if (!load_image(sm.img, a.image, a.image_bytes, sm.mbar, 0)) {
+      if (threadIdx.x == 0) atomicExch(&a.g->error, 3);
+      return;
+    }
   }
   if (threadIdx.x == 0 && blockIdx.x == 0 && a.g->t0 == 0)
     atomicCAS(&a.g->t0, 0ull, static_cast<unsigned long long>(eps_now_ns()));
   const Team tm = eps_team(a, team_id);
-  const Tab tb = make_tab(sm.img);
+  const Tab tb = make_tab(a.table_global ? a.image : sm.img);
   const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
   EpsCtrl* sc = sm.sc;

@@ -77,8 +77,9 @@ struct SolveArgs {
   int obj_ub;
   int64_t node_limit;
   int64_t time_limit_ns;
-  uint32_t max_image_bytes;
+  uint32_t max_image_bytes;  // 0 when the tables are read from global memory
   int max_track_words;
+  int table_global;
 };
 
 // Broadcast slots of one team's search.  Each slot has one writer (thread 0)
@@ -291,15 +292,19 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
     const int i = sc->next;
     if (i >= a.n_inst) break;
     const InstanceDesc d = a.inst[i];
-    if (!load_image(img, d.image, d.image_bytes, mbar, parity)) {
-      if (threadIdx.x == 0) {
-        a.res[i].status = PCCP_RES_LIMIT;
-        a.res[i].error = 3;
+    if (!a.table_global) {
+      if (!load_image(img, d.image, d.image_bytes, mbar, parity)) {
+        if (threadIdx.x == 0) {
+          a.res[i].status = PCCP_RES_LIMIT;
+          a.res[i].error = 3;
+        }
+        return;
       }
-      return;
+      parity ^= 1u;
+    } else {
+      __syncthreads();
     }
-    parity ^= 1u;
-    const Tab tb = make_tab(img);
+    const Tab tb = make_tab(a.table_global ? d.image : img);
     const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
     team_dfs<kTrack>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter, a.witness + d.witness_off,
                      &a.res[i]);
@@ -527,6 +532,15 @@ size_t solve_smem(uint32_t max_img, int max_track_words, int max_vars) {
          static_cast<size_t>(max_vars) * sizeof(int2);
 }
 
+// Shared memory of k_solve, with the tables in shared memory when they fit,
+// else read from the device images (*global = true).
+size_t plan_solve_smem(uint32_t max_img, int max_track_words, int max_vars, int smem_max,
+                       bool* global) {
+  const size_t with = solve_smem(max_img, max_track_words, max_vars);
+  *global = with > static_cast<size_t>(smem_max);
+  return *global ? solve_smem(0, max_track_words, max_vars) : with;
+}
+
 int max_dyn_smem() {
   int dev = 0, v = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
@@ -558,6 +572,7 @@ int check_device(const pccp_model* m) {
 
 struct PropPlan {
   void (*kern)(PropArgs);
+  bool table_global;
   int team, teams, grid;
   size_t smem;
 };
@@ -569,10 +584,15 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
   int team = (cfg && cfg->team_threads > 0) ? cfg->team_threads : 128;
   if (team % 32 != 0 || team > 1024) return PCCP_ERR_INVALID;
-  const size_t base = static_cast<size_t>(m->image_bytes) + 16;
   const size_t per_team = sizeof(PropCtrl) + 4 * ((track_words(m->n_vars, m->n_lin) + 3) & ~3) +
                           static_cast<size_t>(m->n_vars) * sizeof(int2);
+  // the table lives in shared memory when it fits beside one team's store;
+  // otherwise every CTA reads it from the device image (through L1 / L2)
+  const bool global = static_cast<size_t>(m->image_bytes) + 16 + per_team >
+                      static_cast<size_t>(smem_max);
+  const size_t base = (global ? 0 : static_cast<size_t>(m->image_bytes)) + 16;
   if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
+  if (global && !(cfg && cfg->team_threads > 0)) team = 1024;
   int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
   // default: 4 teams of 128 threads per CTA, three CTAs per SM (48 warps)
   int teams = (cfg && cfg->teams_per_cta > 0) ? cfg->teams_per_cta : 4;
@@ -600,6 +620,7 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   if (cfg && cfg->ctas_per_sm > 0) per_sm = std::min(per_sm, static_cast<int>(cfg->ctas_per_sm));
   const int want = (n_stores + teams - 1) / teams;
   p->kern = kern;
+  p->table_global = global;
   p->team = team;
   p->teams = teams;
   p->grid = std::max(1, std::min(want, sms * per_sm));
@@ -730,6 +751,7 @@ int pccp_propagate_ex(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_
   a.max_iter = (cfg && cfg->max_iterations > 0) ? cfg->max_iterations : m->max_iter;
   a.track_words = track_words(m->n_vars, m->n_lin);
   a.work = work;
+  a.table_global = plan.table_global ? 1 : 0;
   plan.kern<<<plan.grid, plan.team * plan.teams, plan.smem, s>>>(a);
   const cudaError_t le = cudaGetLastError();
   cudaFreeAsync(counter, s);
@@ -778,8 +800,10 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     max_branch = std::max(max_branch, m->n_branch);
     max_tw = std::max(max_tw, track_words(m->n_vars, m->n_lin));
   }
-  const size_t smem = solve_smem(max_img, max_tw, max_vars);
+  bool global = false;
+  const size_t smem = plan_solve_smem(max_img, max_tw, max_vars, smem_max, &global);
   if (smem > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
+  if (global && opts->threads <= 0) threads = 1024;
   const auto ksolve = opts->skip_stable ? k_solve<true> : k_solve<false>;
   PCCP_CUDA(cudaFuncSetAttribute(ksolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
@@ -828,8 +852,9 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     a.obj_ub = opts->obj_ub;
     a.node_limit = opts->node_limit;
     a.time_limit_ns = opts->time_limit_ms > 0 ? opts->time_limit_ms * 1000000ll : 0;
-    a.max_image_bytes = max_img;
+    a.max_image_bytes = global ? 0 : max_img;
     a.max_track_words = max_tw;
+    a.table_global = global ? 1 : 0;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
       rc = PCCP_ERR_CUDA;
       break;
@@ -893,12 +918,15 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   const int smem_max = max_dyn_smem();
   const int sms = sm_count();
   if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
-  const int team = o->threads > 0 ? o->threads : 128;
+  int team = o->threads > 0 ? o->threads : 128;
   if (team % 32 != 0 || team > 1024) return PCCP_ERR_INVALID;
-  const size_t base = static_cast<size_t>(m->image_bytes) + 16;
   const size_t per_team = sizeof(EpsCtrl) + 4 * ((track_words(m->n_vars, m->n_lin) + 3) & ~3) +
                           static_cast<size_t>(m->n_vars) * sizeof(int2);
+  const bool global = static_cast<size_t>(m->image_bytes) + 16 + per_team >
+                      static_cast<size_t>(smem_max);
+  const size_t base = (global ? 0 : static_cast<size_t>(m->image_bytes)) + 16;
   if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
+  if (global && o->threads <= 0) team = 1024;
   const int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
   const int teams = std::max(1, std::min({8, fit, 1024 / team}));
   const size_t smem = base + static_cast<size_t>(teams) * per_team;
@@ -969,6 +997,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     a.strategy = o->strategy;
     a.obj_ub = o->obj_ub;
     a.track_words = track_words(m->n_vars, m->n_lin);
+    a.table_global = global ? 1 : 0;
     a.node_limit = o->node_limit;
     a.time_limit_ns = o->time_limit_ms > 0 ? o->time_limit_ms * 1000000ll : 0;
     uint8_t* lin = d + o_la;
