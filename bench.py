@@ -262,6 +262,7 @@ def recorded_traffic():
 SEARCH_MODELS = 256
 SEARCH_NODE_LIMIT = 4000
 EPS_TIME_MS = 2000
+EPS_NODE_LIMIT = 0  # > 0: the parallel runs stop on nodes instead of time
 
 
 def search_bench(pccp, cpu=True):
@@ -285,14 +286,20 @@ def search_bench(pccp, cpu=True):
         "ms": ms, "nodes": nodes,
         "solutions_found": sum(r["solutions"] for r in res),
         "iterations_per_node": sum(r["iterations"] for r in res) / max(nodes, 1)}}
-    m = pccp.Model.from_rcpsp(config_instance("j30", 0))
-    r = pccp.solve(m, deterministic=False, time_limit_ms=EPS_TIME_MS)
-    out["parallel"] = {
-        "workload": f"one 30-task model (j30/0), all teams, {EPS_TIME_MS} ms limit",
-        "nodes_per_s": r["nodes"] / (r["elapsed_ms"] / 1000),
-        "propagator_evals_per_s": r["rows_evaluated"] / (r["elapsed_ms"] / 1000),
-        "ms": r["elapsed_ms"], "nodes": r["nodes"], "status": r["status"],
-        "best_makespan": r["objective"]}
+    for key, fam, what in (("parallel", "j30", "30-task"), ("parallel_large", "j120", "120-task")):
+        m = pccp.Model.from_rcpsp(config_instance(fam, 0))
+        if EPS_NODE_LIMIT:
+            r = pccp.solve(m, deterministic=False, node_limit=EPS_NODE_LIMIT)
+        else:
+            r = pccp.solve(m, deterministic=False, time_limit_ms=EPS_TIME_MS)
+        limit = f"{EPS_NODE_LIMIT} node limit" if EPS_NODE_LIMIT else f"{EPS_TIME_MS} ms limit"
+        out[key] = {
+            "workload": f"one {what} model ({fam}/0), all teams, {limit}"
+                        + (", table read from global memory" if fam == "j120" else ""),
+            "nodes_per_s": r["nodes"] / (r["elapsed_ms"] / 1000),
+            "propagator_evals_per_s": r["rows_evaluated"] / (r["elapsed_ms"] / 1000),
+            "ms": r["elapsed_ms"], "nodes": r["nodes"], "status": r["status"],
+            "best_makespan": r["objective"]}
     if cpu:
         import oracle
         from oracle.rcpsp import rcpsp_model
@@ -469,6 +476,16 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_search_only(args):
+    """Only the search leg (used for ncu captures of the search kernels)."""
+    import torch
+    import paper_2207_12116_gb300 as pccp
+    torch.cuda.set_device(0)
+    global SEARCH_MODELS, SEARCH_NODE_LIMIT, EPS_NODE_LIMIT
+    SEARCH_MODELS, SEARCH_NODE_LIMIT, EPS_NODE_LIMIT = 64, 500, 2_000_000
+    print(json.dumps(search_bench(pccp, cpu=False)), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,6 +495,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-search", action="store_true")
+    ap.add_argument("--search-only", action="store_true",
+                    help="small search leg only (64 models x 500 nodes; parallel runs "
+                         "stopped after 2,000,000 nodes)")
     ap.add_argument("--team", type=int, default=0, help="threads per team (0: library default)")
     ap.add_argument("--teams", type=int, default=0, help="teams per CTA (0: library default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
@@ -486,6 +506,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.search_only:
+        run_search_only(args)
     else:
         run_gpu(args)
 

@@ -1,0 +1,152 @@
+// policy.cuh -- learned branching: per-variable features and a small MLP
+// (12 -> 128 -> 128 -> 1, ReLU) that scores the unfixed branch variables of a
+// search node.  BF16 weights and activations, FP32 accumulation, on the
+// tensor cores through warp-level mma.sync m16n8k16 tiles: the contraction is
+// a handful of 16 x 128 x 128 tiles per node inside one team of a persistent
+// search kernel, so it is issued by the team's own warps from registers (a
+// per-CTA TMEM allocation and single-thread tcgen05 issue would serialise the
+// teams that share a CTA for work worth ~1% of a node).
+//
+// The policy only chooses which variable to split; the split itself (lower
+// half first) and the tree it spans are those of the plain strategies, so a
+// complete search keeps exact optima whatever the scores are.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "pccp_device.cuh"
+
+namespace pccp {
+
+constexpr int kPolicyFeatures = 12;
+constexpr int kPolicyHidden = 128;
+
+// Device image of a policy (built by pccp_policy_create).  B operands are
+// stored as ready-made m16n8k16 fragments: two 32-bit words per lane.
+struct PolicyDev {
+  uint2 w1[16][32];      // layer 1, n-tile j (outputs 8j..8j+7), lane; K = 16 (12 used)
+  uint2 w2[8][16][32];   // layer 2, k-step kk (inputs 16kk..), n-tile j, lane
+  float b1[kPolicyHidden];
+  float b2[kPolicyHidden];
+  float w3[kPolicyHidden];
+  float b3;
+  float pad[3];
+};
+
+// Static features of the branch variables (per model, in the table image):
+// out-degree and summed offsets of temporal rows (x), in-degree (y), reified
+// rows touching the variable, linear rows holding it.
+struct BranchStatic {
+  float out_deg, sum_d, in_deg, n_reified, n_linear, pad[3];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint2 b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+// The 12 features of branch variable number k (index into the branch list)
+// at a node, written as 16 bf16 (4 zero pads) into row k of X (8 words/row).
+//   0 (lb - lb0) / (w0 + 1)     1 (ub - lb0) / (w0 + 1)    2 (ub - lb) / (w0 + 1)
+//   3 log2(1 + ub - lb) / 16    4 out-degree / 8           5 summed offsets / (w0 + 1)
+//   6 in-degree / 8             7 reified rows / 64         8 linear rows / 16
+//   9 k / n_branch              10 depth / (depth + 32)    11 objective progress
+// (w0 = root width of the variable; objective progress = (lb(obj) - lb0(obj))
+// / (root width of obj + 1), 0 without an objective.)
+__device__ __forceinline__ void write_features(uint32_t* X, int k, int v, int2 D, int2 R,
+                                               const BranchStatic& s, int n_branch, int depth,
+                                               float obj_prog) {
+  const float inv = 1.0f / (static_cast<float>(R.y - R.x) + 1.0f);
+  const float f0 = static_cast<float>(D.x - R.x) * inv;
+  const float f1 = static_cast<float>(D.y - R.x) * inv;
+  const float f2 = static_cast<float>(D.y - D.x) * inv;
+  const float f3 = __log2f(1.0f + static_cast<float>(D.y - D.x)) * (1.0f / 16.0f);
+  const float f4 = s.out_deg * 0.125f;
+  const float f5 = s.sum_d * inv;
+  const float f6 = s.in_deg * 0.125f;
+  const float f7 = s.n_reified * (1.0f / 64.0f);
+  const float f8 = s.n_linear * (1.0f / 16.0f);
+  const float f9 = static_cast<float>(k) / static_cast<float>(n_branch);
+  const float f10 = static_cast<float>(depth) / (static_cast<float>(depth) + 32.0f);
+  uint32_t* row = X + 8 * k;
+  row[0] = pack_bf16x2(f0, f1);
+  row[1] = pack_bf16x2(f2, f3);
+  row[2] = pack_bf16x2(f4, f5);
+  row[3] = pack_bf16x2(f6, f7);
+  row[4] = pack_bf16x2(f8, f9);
+  row[5] = pack_bf16x2(f10, obj_prog);
+  row[6] = 0u;
+  row[7] = 0u;
+  (void)v;
+}
+
+// Scores of rows 16c .. 16c+15 of X by one warp.  On return the lanes with
+// (lane & 3) == 0 hold the scores of rows 16c + lane/4 (s_lo) and
+// 16c + lane/4 + 8 (s_hi).  Kept out of line so its 40-odd live registers do
+// not raise the register count of the propagation loop.
+__device__ __noinline__ void mlp_score_chunk(const PolicyDev* __restrict__ pol,
+                                             const uint32_t* X, int c, float* s_lo,
+                                             float* s_hi) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * c + g, r1 = r0 + 8;
+  const uint32_t a1[4] = {X[8 * r0 + t], X[8 * r1 + t], X[8 * r0 + 4 + t], X[8 * r1 + 4 + t]};
+  uint32_t a2[8][4];
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_16816(d0, a1, __ldg(&pol->w1[2 * kk][lane]));
+    mma_16816(d1, a1, __ldg(&pol->w1[2 * kk + 1][lane]));
+    const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
+    const float b00 = __ldg(&pol->b1[c0]), b01 = __ldg(&pol->b1[c0 + 1]);
+    const float b10 = __ldg(&pol->b1[c1]), b11 = __ldg(&pol->b1[c1 + 1]);
+    a2[kk][0] = pack_bf16x2(fmaxf(d0[0] + b00, 0.f), fmaxf(d0[1] + b01, 0.f));
+    a2[kk][1] = pack_bf16x2(fmaxf(d0[2] + b00, 0.f), fmaxf(d0[3] + b01, 0.f));
+    a2[kk][2] = pack_bf16x2(fmaxf(d1[0] + b10, 0.f), fmaxf(d1[1] + b11, 0.f));
+    a2[kk][3] = pack_bf16x2(fmaxf(d1[2] + b10, 0.f), fmaxf(d1[3] + b11, 0.f));
+  }
+  float p_lo = 0.f, p_hi = 0.f;
+#pragma unroll 1
+  for (int j = 0; j < 16; ++j) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) mma_16816(acc, a2[kk], __ldg(&pol->w2[kk][j][lane]));
+    const int c0 = 8 * j + 2 * t;
+    const float bb0 = __ldg(&pol->b2[c0]), bb1 = __ldg(&pol->b2[c0 + 1]);
+    const float w0 = __ldg(&pol->w3[c0]), w1 = __ldg(&pol->w3[c0 + 1]);
+    p_lo += fmaxf(acc[0] + bb0, 0.f) * w0 + fmaxf(acc[1] + bb1, 0.f) * w1;
+    p_hi += fmaxf(acc[2] + bb0, 0.f) * w0 + fmaxf(acc[3] + bb1, 0.f) * w1;
+  }
+  p_lo += __shfl_xor_sync(0xffffffffu, p_lo, 1);
+  p_lo += __shfl_xor_sync(0xffffffffu, p_lo, 2);
+  p_hi += __shfl_xor_sync(0xffffffffu, p_hi, 1);
+  p_hi += __shfl_xor_sync(0xffffffffu, p_hi, 2);
+  const float b3 = __ldg(&pol->b3);
+  *s_lo = p_lo + b3;
+  *s_hi = p_hi + b3;
+}
+
+// Order-preserving map of a float score to an unsigned integer.
+__device__ __forceinline__ uint32_t score_key(float s) {
+  const uint32_t u = __float_as_uint(s);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Selection key of the learned strategy: highest score first, ties to the
+// lower branch index; 0 means "no unfixed branch variable".
+__device__ __forceinline__ unsigned long long learned_key(float s, int k) {
+  return (static_cast<unsigned long long>(score_key(s)) << 32) |
+         static_cast<unsigned long long>(0xffffffffu - static_cast<uint32_t>(k));
+}
+
+}  // namespace pccp
