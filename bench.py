@@ -486,6 +486,55 @@ def run_search_only(args):
     print(json.dumps(search_bench(pccp, cpu=False)), flush=True)
 
 
+def run_learned(args):
+    """Learned branching against plain first-fail on 64 seeded 60-task models
+    (one persistent launch each, same limits, same GPU).  The policy is
+    trained first on nodes of the 8-task and 30-task families."""
+    import torch
+    import paper_2207_12116_gb300 as pccp
+    from paper_2207_12116_gb300 import learn
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    train_insts = [config_instance("tiny8", s) for s in range(64)] + \
+                  [config_instance("j30", s) for s in range(16)]
+    data = learn.collect(train_insts, nodes_per_model=256, seed=7)
+    pol = pccp.Policy.random(0)
+    losses = learn.train(pol, data, epochs=args.learned_epochs, groups_per_batch=256, lr=2e-3)
+    acc = learn.ranking_accuracy(pol, data)
+    t_train = time.perf_counter() - t0
+    models = [pccp.Model.from_rcpsp(config_instance("j60", 1000 + s)) for s in range(64)]
+    out = {}
+    for name, kw in (("first_fail", {"strategy": pccp.PCCP_FIRST_FAIL}),
+                     ("learned", {"strategy": pccp.PCCP_LEARNED, "policy": pol})):
+        res = pccp.solve_batch(models, node_limit=args.learned_nodes,
+                               time_limit_ms=args.learned_ms, **kw)
+        proven = [r for r in res if r["status"] != pccp.PCCP_RES_LIMIT]
+        out[name] = {
+            "kernel_ms": res[0]["elapsed_ms"], "nodes": sum(r["nodes"] for r in res),
+            "proven_optimal_or_infeasible": len(proven),
+            "nodes_to_proof_mean": (float(np.mean([r["nodes"] for r in proven]))
+                                    if proven else None),
+            "with_solution": sum(r["has_solution"] for r in res),
+            "mean_best_makespan": float(np.mean([r["objective"] for r in res
+                                                 if r["has_solution"]] or [float("nan")])),
+            "best_makespans": [r["objective"] for r in res]}
+    both = [(a, b) for a, b in zip(out["first_fail"]["best_makespans"],
+                                   out["learned"]["best_makespans"])
+            if a is not None and b is not None]
+    line = {"metric": "time and nodes to proven optimum, learned vs first-fail",
+            "workload": f"64 seeded 60-task 4-resource models, one launch per strategy, "
+                        f"{args.learned_nodes} nodes and {args.learned_ms} ms per model",
+            "training": {"groups": int(data["group_off"].numel() - 1),
+                         "rows": int(data["features"].shape[0]), "epochs": args.learned_epochs,
+                         "loss_first_last": [losses[0], losses[-1]],
+                         "probe_top1_accuracy": acc, "seconds": t_train},
+            "first_fail": {k: v for k, v in out["first_fail"].items() if k != "best_makespans"},
+            "learned": {k: v for k, v in out["learned"].items() if k != "best_makespans"},
+            "learned_better_equal_worse": [sum(b < a for a, b in both), sum(b == a for a, b in both),
+                                           sum(b > a for a, b in both)]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -495,6 +544,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-search", action="store_true")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned branching vs first-fail on 64 60-task models (own JSON line)")
+    ap.add_argument("--learned-epochs", type=int, default=8)
+    ap.add_argument("--learned-nodes", type=int, default=20000)
+    ap.add_argument("--learned-ms", type=int, default=20000)
     ap.add_argument("--search-only", action="store_true",
                     help="small search leg only (64 models x 500 nodes; parallel runs "
                          "stopped after 2,000,000 nodes)")
@@ -508,6 +562,8 @@ def main():
         run_reference(args)
     elif args.search_only:
         run_search_only(args)
+    elif args.learned:
+        run_learned(args)
     else:
         run_gpu(args)
 

@@ -165,6 +165,9 @@ int pccp_propagate_ex(const pccp_model* model, int32_t n_stores, int32_t* lb, in
 
 #define PCCP_INPUT_ORDER 0 /* lowest-index unfixed branch variable */
 #define PCCP_FIRST_FAIL 1  /* smallest ub - lb, ties to the lower index */
+#define PCCP_LEARNED 2     /* highest score of a pccp_policy, ties to the lower index */
+
+typedef struct pccp_policy pccp_policy; /* learned branching policy, see below */
 
 #define PCCP_OPTIMISE 0  /* branch and bound on the objective */
 #define PCCP_COUNT_ALL 1 /* enumerate every solution (objective bounded by obj_ub) */
@@ -189,6 +192,7 @@ typedef struct {
   int32_t blocks;        /* CTAs for the parallel search (0 = auto) */
   int32_t skip_stable;   /* as in pccp_launch_config; also lets a left child run
                             only the rows of the decided variable first */
+  const pccp_policy* policy; /* required with PCCP_LEARNED, created on this device */
 } pccp_solve_opts;
 
 /* Counters and outcome of one search.  A node is every store propagated,
@@ -272,6 +276,52 @@ void pccp_batch_destroy(pccp_batch* batch);
 #define PCCP_NOALLOC_SCRATCH_BYTES (8u << 20)
 int pccp_solve_batch_noalloc(const pccp_model* const* models, int32_t n_models,
                              const pccp_solve_opts* opts, pccp_result* results, void* stream);
+
+/* ---- learned branching (no counterpart in the paper) --------------------
+ * A policy is an MLP 12 -> 128 -> 128 -> 1 (ReLU) that scores each unfixed
+ * branch variable of a node from 12 features (its bounds relative to the
+ * root, log width, temporal in/out degree and summed offsets, reified and
+ * linear rows touching it, its input position, the depth and the
+ * objective's progress).  The search splits the highest-scoring variable
+ * (ties to the lower index) with the usual lower-half rule, so a complete
+ * search still proves the same optimum; only the order of the tree changes.
+ * Weights are BF16 on the device (FP32 masters for training); every product
+ * runs on the tensor cores with FP32 accumulation. */
+typedef struct {
+  const float* w1; /* [128][12] */
+  const float* b1; /* [128] */
+  const float* w2; /* [128][128] (out, in) */
+  const float* b2; /* [128] */
+  const float* w3; /* [128] */
+  float b3;
+} pccp_policy_weights;
+
+/* Host weights are copied (synchronous).  Errors: INVALID (NULL or non-finite
+ * weights), CUDA. */
+int pccp_policy_create(const pccp_policy_weights* weights, pccp_policy** out);
+void pccp_policy_destroy(pccp_policy* policy);
+/* Current FP32 weights into caller HOST arrays of the sizes above. */
+int pccp_policy_get_weights(const pccp_policy* policy, float* w1, float* b1, float* w2, float* b2,
+                            float* w3, float* b3);
+/* Features of every branch variable of n_stores stores (DEVICE lb/ub
+ * [n_stores][n_vars], joined with the root; depth DEVICE [n_stores] or NULL
+ * for 0) into DEVICE out [n_stores][n_branch][12], rounded to BF16 as the
+ * network sees them.  Asynchronous. */
+int pccp_policy_features(const pccp_model* model, int32_t n_stores, const int32_t* lb,
+                         const int32_t* ub, const int32_t* depth, float* out, void* stream);
+/* Scores of n_rows DEVICE feature rows [n_rows][12] into DEVICE scores
+ * [n_rows], with the search kernels' arithmetic.  Asynchronous. */
+int pccp_policy_score(const pccp_policy* policy, int32_t n_rows, const float* features,
+                      float* scores, void* stream);
+/* One Adam step (beta 0.9 / 0.999) on the mean listwise softmax
+ * cross-entropy of n_groups groups of candidate rows: DEVICE features
+ * [n_rows][12], DEVICE group_off [n_groups + 1] (rows of group g are
+ * group_off[g] .. group_off[g+1]-1), DEVICE target [n_rows] (a distribution
+ * per group).  *loss (HOST, may be NULL) receives the mean loss before the
+ * step; synchronises the stream when loss != NULL. */
+int pccp_policy_train_step(pccp_policy* policy, int32_t n_rows, const float* features,
+                           const int32_t* group_off, int32_t n_groups, const float* target,
+                           float lr, float* loss, void* stream);
 
 /* Human-readable name of a return code (static storage). */
 const char* pccp_error_string(int code);

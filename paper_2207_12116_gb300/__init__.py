@@ -17,7 +17,8 @@ from . import _abi
 from ._abi import (PCCP_OK, PCCP_ERR_INVALID, PCCP_ERR_OVERFLOW, PCCP_ERR_SMEM,  # noqa: F401
                    PCCP_ERR_TIMEOUT, PCCP_ERR_CUDA, PCCP_ERR_UNSUPPORTED, PCCP_ERR_SCRATCH,
                    PCCP_FIXPOINT,
-                   PCCP_FAILED, PCCP_ERROR, PCCP_INPUT_ORDER, PCCP_FIRST_FAIL, PCCP_OPTIMISE,
+                   PCCP_FAILED, PCCP_ERROR, PCCP_INPUT_ORDER, PCCP_FIRST_FAIL, PCCP_LEARNED,
+                   PCCP_OPTIMISE,
                    PCCP_COUNT_ALL, PCCP_RES_OPTIMAL, PCCP_RES_INFEASIBLE, PCCP_RES_LIMIT,
                    INT32_MAX, PccpError, check, load, library_path)
 from . import rcpsp  # noqa: F401
@@ -25,7 +26,9 @@ from . import rcpsp  # noqa: F401
 __all__ = ["Model", "pccp_model_create", "pccp_model_destroy", "pccp_model_get_info",
            "pccp_propagate", "pccp_propagate_ex", "pccp_solve", "pccp_solve_batch",
            "pccp_solve_batch_noalloc", "pccp_batch_create", "pccp_batch_solve_async",
-           "pccp_batch_results", "pccp_batch_destroy", "Batch",
+           "pccp_batch_results", "pccp_batch_destroy", "Batch", "Policy",
+           "pccp_policy_create", "pccp_policy_destroy", "pccp_policy_get_weights",
+           "pccp_policy_features", "pccp_policy_score", "pccp_policy_train_step",
            "pccp_error_string", "propagate", "propagate_host", "solve", "solve_batch",
            "PccpError", "load", "library_path"]
 
@@ -235,9 +238,10 @@ def propagate_host(model: Model, lb, ub, device="cuda", config=None, stream=None
 
 
 def _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
-          skip_stable=False):
+          skip_stable=False, policy=None):
     return _abi.pccp_solve_opts(strategy, mode, int(bool(deterministic)), obj_ub, node_limit,
-                                time_limit_ms, threads, blocks, int(bool(skip_stable)))
+                                time_limit_ms, threads, blocks, int(bool(skip_stable)),
+                                policy.handle if policy is not None else None)
 
 
 def _result_dict(r, w):
@@ -251,9 +255,9 @@ def _result_dict(r, w):
 
 def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, deterministic=True,
           obj_ub=INT32_MAX, node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None,
-          skip_stable=False):
+          skip_stable=False, policy=None):
     o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
-              skip_stable)
+              skip_stable, policy)
     w = np.zeros(model.n_vars, dtype=np.int32)
     r = _abi.pccp_result()
     r.witness = w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
@@ -264,11 +268,11 @@ def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, determini
 
 def solve_batch(models, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
                 node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None, noalloc=False,
-                skip_stable=False):
+                skip_stable=False, policy=None):
     """Solve many models in one launch.  noalloc=True uses the allocation-free
     entry point (fixed device scratch; see include/pccp.h)."""
     o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, threads, blocks,
-              skip_stable)
+              skip_stable, policy)
     n = len(models)
     ws = [np.zeros(m.n_vars, dtype=np.int32) for m in models]
     res = (_abi.pccp_result * n)()
@@ -292,8 +296,9 @@ class Batch:
         self._ws = [np.zeros(m.n_vars, dtype=np.int32) for m in self.models]
 
     def solve_async(self, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
-                    node_limit=0, time_limit_ms=0, stream=None, skip_stable=False):
-        o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, 0, 0, skip_stable)
+                    node_limit=0, time_limit_ms=0, stream=None, skip_stable=False, policy=None):
+        o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, 0, 0, skip_stable,
+                  policy)
         check(pccp_batch_solve_async(self.handle, o, _stream_ptr(stream)), "pccp_batch_solve_async")
 
     def results(self, stream=None):
@@ -314,3 +319,114 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------- learned branching
+
+def pccp_policy_create(weights):
+    h = ctypes.c_void_p()
+    rc = load().pccp_policy_create(ctypes.byref(weights), ctypes.byref(h))
+    return rc, h
+
+
+def pccp_policy_destroy(handle):
+    load().pccp_policy_destroy(handle)
+
+
+def pccp_policy_get_weights(handle, w1, b1, w2, b2, w3, b3):
+    return load().pccp_policy_get_weights(handle, w1, b1, w2, b2, w3, b3)
+
+
+def pccp_policy_features(model_handle, n, lb, ub, depth, out, stream):
+    return load().pccp_policy_features(model_handle, n, lb, ub, depth, out, stream)
+
+
+def pccp_policy_score(handle, n, features, scores, stream):
+    return load().pccp_policy_score(handle, n, features, scores, stream)
+
+
+def pccp_policy_train_step(handle, n_rows, features, group_off, n_groups, target, lr, loss, stream):
+    return load().pccp_policy_train_step(handle, n_rows, features, group_off, n_groups, target,
+                                         lr, loss, stream)
+
+
+POLICY_SHAPES = {"w1": (128, 12), "b1": (128,), "w2": (128, 128), "b2": (128,), "w3": (128,)}
+
+
+class Policy:
+    """A learned branching policy on the device (MLP 12 -> 128 -> 128 -> 1)."""
+
+    def __init__(self, weights):
+        arr = {k: np.ascontiguousarray(np.asarray(weights[k], dtype=np.float32).reshape(shape))
+               for k, shape in POLICY_SHAPES.items()}
+        self._host = arr
+        w = _abi.pccp_policy_weights(*[ctypes.c_void_p(arr[k].ctypes.data)
+                                       for k in ("w1", "b1", "w2", "b2", "w3")],
+                                     float(weights["b3"]))
+        rc, h = pccp_policy_create(w)
+        check(rc, "pccp_policy_create")
+        self.handle = h
+
+    @classmethod
+    def random(cls, seed=0, scale=1.0):
+        """He-initialised weights from a seeded generator."""
+        g = np.random.default_rng(seed)
+        return cls({"w1": g.normal(0, scale * np.sqrt(2 / 12), (128, 12)),
+                    "b1": np.zeros(128), "w2": g.normal(0, scale * np.sqrt(2 / 128), (128, 128)),
+                    "b2": np.zeros(128), "w3": g.normal(0, scale * np.sqrt(1 / 128), 128),
+                    "b3": 0.0})
+
+    def weights(self):
+        out = {k: np.zeros(shape, dtype=np.float32) for k, shape in POLICY_SHAPES.items()}
+        b3 = np.zeros(1, dtype=np.float32)
+        rc = pccp_policy_get_weights(self.handle, *[ctypes.c_void_p(out[k].ctypes.data)
+                                                    for k in ("w1", "b1", "w2", "b2", "w3")],
+                                     ctypes.c_void_p(b3.ctypes.data))
+        check(rc, "pccp_policy_get_weights")
+        out["b3"] = float(b3[0])
+        return out
+
+    def score(self, features, stream=None):
+        """Scores of feature rows (float32 CUDA tensor [n, 12]) -> CUDA tensor [n]."""
+        import torch
+        f = features.contiguous()
+        s = torch.empty(f.shape[0], dtype=torch.float32, device=f.device)
+        check(pccp_policy_score(self.handle, f.shape[0], ctypes.c_void_p(f.data_ptr()),
+                                ctypes.c_void_p(s.data_ptr()), _stream_ptr(stream)),
+              "pccp_policy_score")
+        return s
+
+    def train_step(self, features, group_off, target, lr=1e-3, stream=None):
+        """One Adam step on the mean listwise cross-entropy; returns the loss."""
+        loss = ctypes.c_float(0.0)
+        f = features.contiguous()
+        go = group_off.contiguous()
+        t = target.contiguous()
+        check(pccp_policy_train_step(self.handle, f.shape[0], ctypes.c_void_p(f.data_ptr()),
+                                     ctypes.c_void_p(go.data_ptr()), go.shape[0] - 1,
+                                     ctypes.c_void_p(t.data_ptr()), lr, ctypes.byref(loss),
+                                     _stream_ptr(stream)), "pccp_policy_train_step")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            pccp_policy_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def policy_features(model: Model, lb, ub, depth=None, stream=None):
+    """Features [n, n_branch, 12] (float32 CUDA) of stores lb/ub [n, n_vars]."""
+    import torch
+    n = lb.shape[0]
+    out = torch.empty((n, len(model.branch), 12), dtype=torch.float32, device=lb.device)
+    dp = ctypes.c_void_p(depth.data_ptr()) if depth is not None else ctypes.c_void_p(0)
+    check(pccp_policy_features(model.handle, n, ctypes.c_void_p(lb.data_ptr()),
+                               ctypes.c_void_p(ub.data_ptr()), dp, ctypes.c_void_p(out.data_ptr()),
+                               _stream_ptr(stream)), "pccp_policy_features")
+    return out

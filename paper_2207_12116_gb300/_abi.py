@@ -22,7 +22,7 @@ PCCP_ERR_UNSUPPORTED = -6
 PCCP_ERR_SCRATCH = -7
 
 PCCP_FIXPOINT, PCCP_FAILED, PCCP_ERROR = 0, 1, 2
-PCCP_INPUT_ORDER, PCCP_FIRST_FAIL = 0, 1
+PCCP_INPUT_ORDER, PCCP_FIRST_FAIL, PCCP_LEARNED = 0, 1, 2
 PCCP_OPTIMISE, PCCP_COUNT_ALL = 0, 1
 PCCP_RES_OPTIMAL, PCCP_RES_INFEASIBLE, PCCP_RES_LIMIT = 0, 1, 2
 INT32_MAX = (1 << 31) - 1
@@ -56,7 +56,11 @@ class pccp_launch_config(ctypes.Structure):
 class pccp_solve_opts(ctypes.Structure):
     _fields_ = [("strategy", I32), ("mode", I32), ("deterministic", I32), ("obj_ub", I32),
                 ("node_limit", I64), ("time_limit_ms", I64), ("threads", I32), ("blocks", I32),
-                ("skip_stable", I32)]
+                ("skip_stable", I32), ("policy", P)]
+
+
+class pccp_policy_weights(ctypes.Structure):
+    _fields_ = [("w1", P), ("b1", P), ("w2", P), ("b2", P), ("w3", P), ("b3", ctypes.c_float)]
 
 
 class pccp_result(ctypes.Structure):
@@ -82,6 +86,13 @@ SIGNATURES = {
     "pccp_batch_solve_async": (ctypes.c_int, [P, ctypes.POINTER(pccp_solve_opts), P]),
     "pccp_batch_results": (ctypes.c_int, [P, ctypes.POINTER(pccp_result), P]),
     "pccp_batch_destroy": (None, [P]),
+    "pccp_policy_create": (ctypes.c_int, [ctypes.POINTER(pccp_policy_weights), ctypes.POINTER(P)]),
+    "pccp_policy_destroy": (None, [P]),
+    "pccp_policy_get_weights": (ctypes.c_int, [P, P, P, P, P, P, P]),
+    "pccp_policy_features": (ctypes.c_int, [P, I32, P, P, P, P, P]),
+    "pccp_policy_score": (ctypes.c_int, [P, I32, P, P, P]),
+    "pccp_policy_train_step": (ctypes.c_int, [P, I32, P, P, I32, P, ctypes.c_float,
+                                              ctypes.POINTER(ctypes.c_float), P]),
     "pccp_error_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
 

@@ -12,6 +12,7 @@
 #pragma once
 
 #include "pccp_device.cuh"
+#include "policy.cuh"
 
 namespace pccp {
 
@@ -54,6 +55,8 @@ struct EpsArgs {
   int obj_ub;
   int track_words;
   int table_global;  // 1: rows are read from the device image
+  int x_words;       // learned strategy: feature rows per team (words)
+  const PolicyDev* policy;
   int64_t node_limit;
   int64_t time_limit_ns;
 };
@@ -67,7 +70,8 @@ struct EpsCtrl {
   int depth;
   int next;
   int out;
-  int pad[2];
+  int cur_depth;  // P1: depth of the node (features of the learned strategy)
+  int pad;
 };
 
 enum : int { kNodeFailed = 0, kNodeSolution = 1, kNodeBranch = 2, kNodeStop = 3, kNodeError = 4 };
@@ -90,10 +94,11 @@ __device__ __forceinline__ uint64_t eps_now_ns() {
 // the selection key (branch index in the low 32 bits).  Team-uniform result.
 // Broadcast slots follow the protocol of team_dfs: written before a barrier,
 // read after it, not rewritten before another barrier has passed.
-template <bool kTrack>
+template <bool kTrack, bool kLearned>
 __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm, EpsCtrl* sc,
                                         const Track& tk, bool seeded, unsigned par,
-                                        const EpsArgs& a, int& it, unsigned long long& key) {
+                                        const EpsArgs& a, int& it, unsigned long long& key,
+                                        int depth, uint32_t* X) {
   EpsGlobal* g = a.g;
   if (tm.tid == 0) {
     int stop = ld_relaxed_gpu(&g->stop);
@@ -121,6 +126,7 @@ __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm,
     sc->fc.evals = 0;
     sc->fc.bytes = 0;
     sc->sel[par] = ~0ull;
+    sc->cur_depth = depth;
   }
   team_bar(tm.bar, tm.nthr);
   if (sc->stop) return kNodeStop;
@@ -128,15 +134,19 @@ __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm,
   if (fst == kError) return kNodeError;
   if (fst == kFailed) return kNodeFailed;
   unsigned long long* sel = &sc->sel[par];
-  for (int k = tm.tid; k < tb.n_branch; k += tm.nthr) {
-    const int v = tb.branch[k];
-    const int2 D = ld_dom(st, v);
-    if (D.x < D.y) {
-      unsigned long long kk = static_cast<unsigned long long>(k);
-      if (a.strategy == PCCP_FIRST_FAIL)
-        kk |= static_cast<unsigned long long>(static_cast<uint32_t>(D.y - D.x)) << 32;
-      atomicMin(sel, kk);
-      if (a.strategy == PCCP_INPUT_ORDER) break;
+  if (kLearned) {
+    learned_select(tb, st, a.root, tm, a.policy, X, sel, sc->cur_depth);
+  } else {
+    for (int k = tm.tid; k < tb.n_branch; k += tm.nthr) {
+      const int v = tb.branch[k];
+      const int2 D = ld_dom(st, v);
+      if (D.x < D.y) {
+        unsigned long long kk = static_cast<unsigned long long>(k);
+        if (a.strategy == PCCP_FIRST_FAIL)
+          kk |= static_cast<unsigned long long>(static_cast<uint32_t>(D.y - D.x)) << 32;
+        atomicMin(sel, kk);
+        if (a.strategy == PCCP_INPUT_ORDER) break;
+      }
     }
   }
   if (kTrack) track_clear02(tk, tm);  // for a left child's seeded fixed point
@@ -213,6 +223,7 @@ struct EpsSmem {
   EpsCtrl* sc;
   uint32_t* track;
   int2* st;
+  uint32_t* X;  // learned strategy's feature rows
 };
 
 __device__ __forceinline__ EpsSmem eps_smem(uint8_t* smem, const EpsArgs& a, int team_id) {
@@ -228,6 +239,8 @@ __device__ __forceinline__ EpsSmem eps_smem(uint8_t* smem, const EpsArgs& a, int
   s.track = track_base + static_cast<size_t>(tw16) * team_id;
   int2* st_base = reinterpret_cast<int2*>(track_base + static_cast<size_t>(tw16) * a.teams);
   s.st = st_base + static_cast<size_t>(team_id) * a.n_vars;
+  uint32_t* x_base = reinterpret_cast<uint32_t*>(st_base + static_cast<size_t>(a.teams) * a.n_vars);
+  s.X = x_base + static_cast<size_t>(team_id) * a.x_words;
   return s;
 }
 
@@ -245,7 +258,7 @@ __device__ __forceinline__ Team eps_team(const EpsArgs& a, int team_id) {
 // One breadth-first level: every input path is propagated once; failures
 // and solutions are counted; every other node pushes its two children
 // (left ub <= m, right lb >= m + 1) to the output level.
-template <bool kTrack>
+template <bool kTrack, bool kLearned>
 __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
@@ -276,7 +289,7 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
     eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, tk, path, a.in_len);
     int it = 0;
     unsigned long long key = 0;
-    const int r = eps_node<kTrack>(tb, sm.st, tm, sc, tk, false, par, a, it, key);
+    const int r = eps_node<kTrack, kLearned>(tb, sm.st, tm, sc, tk, false, par, a, it, key, a.in_len, sm.X);
     par ^= 1u;
     if (r == kNodeStop) break;
     if (tm.tid == 0) {
@@ -335,7 +348,7 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
 }
 
 // Persistent teams search the subtrees under the frontier paths depth first.
-template <bool kTrack>
+template <bool kTrack, bool kLearned>
 __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
@@ -373,7 +386,7 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
     for (;;) {
       int it = 0;
       unsigned long long key = 0;
-      const int r = eps_node<kTrack>(tb, sm.st, tm, sc, tk, seeded, par, a, it, key);
+      const int r = eps_node<kTrack, kLearned>(tb, sm.st, tm, sc, tk, seeded, par, a, it, key, depth, sm.X);
       par ^= 1u;
       if (r == kNodeStop) {
         done = true;

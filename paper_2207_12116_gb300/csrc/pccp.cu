@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -26,6 +27,7 @@
 #include "pccp_device.cuh"
 #include "k_propagate.cuh"
 #include "k_solve_eps.cuh"
+#include "policy_train.cuh"
 
 using namespace pccp;
 
@@ -80,6 +82,9 @@ struct SolveArgs {
   uint32_t max_image_bytes;  // 0 when the tables are read from global memory
   int max_track_words;
   int table_global;
+  int x_words;                // learned strategy: feature rows per team (words)
+  int max_vars_smem;          // store slots reserved per CTA
+  const PolicyDev* policy;
 };
 
 // Broadcast slots of one team's search.  Each slot has one writer (thread 0)
@@ -93,7 +98,8 @@ struct SearchCtrl {
   int err;     // branch path: decision stack overflow
   int depth;   // backtrack: new depth, -1 when the tree is exhausted
   int next;    // next model index (CTA loop)
-  int pad[2];
+  int cur_depth;  // P1: depth of the node (features of the learned strategy)
+  int pad;
 };
 
 constexpr unsigned long long kNoVar = ~0ull;
@@ -105,10 +111,10 @@ constexpr uint32_t kRightBit = 0x80000000u;
 // All control decisions are made by thread 0 and broadcast through shared
 // memory; every broadcast slot is written before a barrier and read after it,
 // and never rewritten before the next barrier that follows all its reads.
-template <bool kTrack>
+template <bool kTrack, bool kLearned>
 __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st, const Team& tm,
                          SearchCtrl* sc, const Track& tk, int2* stack, const SolveArgs& a,
-                         int max_iter, int32_t* witness, InstanceResult* out) {
+                         int max_iter, int32_t* witness, InstanceResult* out, uint32_t* X) {
   const int nv = tb.n_vars;
   const uint64_t t0 = globaltimer_ns();
   // thread-0 state
@@ -144,6 +150,7 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
       sc->fc.evals = 0;
       sc->fc.bytes = 0;
       sc->sel[par] = kNoVar;
+      sc->cur_depth = depth;
     }
     team_bar(tm.bar, tm.nthr);  // N1
     if (sc->stop) break;
@@ -168,15 +175,19 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
     } else {
       // A5: variable selection by a team-wide minimum over branch variables
       unsigned long long* sel = &sc->sel[par];
-      for (int k = tm.tid; k < tb.n_branch; k += tm.nthr) {
-        const int v = tb.branch[k];
-        const int2 D = ld_dom(st, v);
-        if (D.x < D.y) {
-          unsigned long long key = static_cast<unsigned long long>(k);
-          if (a.strategy == PCCP_FIRST_FAIL)
-            key |= static_cast<unsigned long long>(static_cast<uint32_t>(D.y - D.x)) << 32;
-          atomicMin(sel, key);
-          if (a.strategy == PCCP_INPUT_ORDER) break;
+      if (kLearned) {
+        learned_select(tb, st, root, tm, a.policy, X, sel, sc->cur_depth);
+      } else {
+        for (int k = tm.tid; k < tb.n_branch; k += tm.nthr) {
+          const int v = tb.branch[k];
+          const int2 D = ld_dom(st, v);
+          if (D.x < D.y) {
+            unsigned long long key = static_cast<unsigned long long>(k);
+            if (a.strategy == PCCP_FIRST_FAIL)
+              key |= static_cast<unsigned long long>(static_cast<uint32_t>(D.y - D.x)) << 32;
+            atomicMin(sel, key);
+            if (a.strategy == PCCP_INPUT_ORDER) break;
+          }
         }
       }
       if (kTrack) track_clear02(tk, tm);  // for a left child's seeded fixed point
@@ -266,7 +277,7 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
   }
 }
 
-template <bool kTrack>
+template <bool kTrack, bool kLearned>
 __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t* img = smem;
@@ -275,6 +286,7 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
   uint32_t* track_base =
       reinterpret_cast<uint32_t*>(smem + a.max_image_bytes + 16 + sizeof(SearchCtrl));
   int2* st = reinterpret_cast<int2*>(track_base + ((a.max_track_words + 3) & ~3));
+  uint32_t* X = reinterpret_cast<uint32_t*>(st + a.max_vars_smem);
   if (threadIdx.x == 0) mbar_init(mbar, 1);
   Team tm;
   tm.tid = threadIdx.x;
@@ -306,8 +318,8 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
     }
     const Tab tb = make_tab(a.table_global ? d.image : img);
     const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
-    team_dfs<kTrack>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter, a.witness + d.witness_off,
-                     &a.res[i]);
+    team_dfs<kTrack, kLearned>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
+                               a.witness + d.witness_off, &a.res[i], X);
   }
 }
 
@@ -321,6 +333,12 @@ struct Packed {
 
 size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
+}  // namespace
+
+struct pccp_policy;
+namespace {
+int policy_device(const pccp_policy* p);
+const PolicyDev* policy_dev(const pccp_policy* p);
 }  // namespace
 
 struct pccp_model {
@@ -462,6 +480,31 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
     ADJ.insert(ADJ.end(), by_var[v].begin(), by_var[v].end());
     ADJ_OFF[v + 1] = static_cast<int32_t>(ADJ.size());
   }
+  // static features of the branch variables (learned strategy)
+  std::vector<BranchStatic> BST(d->n_branch);
+  {
+    std::vector<float> out_deg(nv, 0.f), sum_d(nv, 0.f), in_deg(nv, 0.f), n_rf(nv, 0.f);
+    for (int32_t i = 0; i < d->n_temporal; ++i) {
+      out_deg[d->temporal[3 * i]] += 1.f;
+      sum_d[d->temporal[3 * i]] += static_cast<float>(d->temporal[3 * i + 2]);
+      in_deg[d->temporal[3 * i + 1]] += 1.f;
+    }
+    for (int32_t i = 0; i < d->n_reified; ++i) {
+      n_rf[d->reified[4 * i + 1]] += 1.f;
+      if (d->reified[4 * i + 2] != d->reified[4 * i + 1]) n_rf[d->reified[4 * i + 2]] += 1.f;
+    }
+    for (int32_t k = 0; k < d->n_branch; ++k) {
+      const int32_t v = d->branch_vars[k];
+      BranchStatic bsk;
+      std::memset(&bsk, 0, sizeof(bsk));
+      bsk.out_deg = out_deg[v];
+      bsk.sum_d = sum_d[v];
+      bsk.in_deg = in_deg[v];
+      bsk.n_reified = n_rf[v];
+      bsk.n_linear = static_cast<float>(by_var[v].size());
+      BST[k] = bsk;
+    }
+  }
 
   TableHeader h;
   std::memset(&h, 0, sizeof(h));
@@ -493,6 +536,8 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   h.off_adj = static_cast<int32_t>(off);
   h.n_adj = static_cast<int32_t>(ADJ.size());
   off = align16(off + ADJ.size() * sizeof(int32_t));
+  h.off_bstat = static_cast<int32_t>(off);
+  off = align16(off + BST.size() * sizeof(BranchStatic));
   if (off > (1u << 30)) return PCCP_ERR_UNSUPPORTED;
   h.image_bytes = static_cast<int32_t>(off);
 
@@ -513,6 +558,8 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   std::memcpy(p->image.data() + h.off_adj_off, ADJ_OFF.data(), ADJ_OFF.size() * sizeof(int32_t));
   if (!ADJ.empty())
     std::memcpy(p->image.data() + h.off_adj, ADJ.data(), ADJ.size() * sizeof(int32_t));
+  if (!BST.empty())
+    std::memcpy(p->image.data() + h.off_bstat, BST.data(), BST.size() * sizeof(BranchStatic));
   p->n_vars = h.n_vars;
   p->n_t = h.n_t;
   p->n_rf = h.n_rf;
@@ -526,19 +573,46 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
 
 // Shared memory of k_solve: table image, mbarrier, control, change
 // tracking, one store.
-size_t solve_smem(uint32_t max_img, int max_track_words, int max_vars) {
+size_t solve_smem(uint32_t max_img, int max_track_words, int max_vars, int x_words = 0) {
   return static_cast<size_t>(max_img) + 16 + sizeof(SearchCtrl) +
          4 * static_cast<size_t>((max_track_words + 3) & ~3) +
-         static_cast<size_t>(max_vars) * sizeof(int2);
+         static_cast<size_t>(max_vars) * sizeof(int2) + 4 * static_cast<size_t>(x_words);
 }
 
 // Shared memory of k_solve, with the tables in shared memory when they fit,
 // else read from the device images (*global = true).
 size_t plan_solve_smem(uint32_t max_img, int max_track_words, int max_vars, int smem_max,
-                       bool* global) {
-  const size_t with = solve_smem(max_img, max_track_words, max_vars);
+                       bool* global, int x_words = 0) {
+  const size_t with = solve_smem(max_img, max_track_words, max_vars, x_words);
   *global = with > static_cast<size_t>(smem_max);
-  return *global ? solve_smem(0, max_track_words, max_vars) : with;
+  return *global ? solve_smem(0, max_track_words, max_vars, x_words) : with;
+}
+
+// Words of shared memory for the learned strategy's feature rows (0 otherwise).
+int policy_x_words(const pccp_solve_opts* o, int max_branch) {
+  return o->strategy == PCCP_LEARNED ? 8 * ((max_branch + 15) & ~15) : 0;
+}
+
+// The k_solve instantiation for a search's options.
+using SolveKernel = void (*)(SolveArgs);
+SolveKernel solve_kernel(const pccp_solve_opts* o) {
+  if (o->strategy == PCCP_LEARNED) return k_solve<false, true>;
+  return o->skip_stable ? k_solve<true, false> : k_solve<false, false>;
+}
+
+// Strategy and policy checks shared by the search entry points.
+int check_strategy(const pccp_solve_opts* o) {
+  if (o->strategy != PCCP_INPUT_ORDER && o->strategy != PCCP_FIRST_FAIL &&
+      o->strategy != PCCP_LEARNED)
+    return PCCP_ERR_INVALID;
+  if (o->mode != PCCP_OPTIMISE && o->mode != PCCP_COUNT_ALL) return PCCP_ERR_INVALID;
+  if (o->strategy == PCCP_LEARNED) {
+    if (!o->policy) return PCCP_ERR_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PCCP_ERR_CUDA;
+    if (dev != policy_device(o->policy)) return PCCP_ERR_INVALID;
+  }
+  return PCCP_OK;
 }
 
 int max_dyn_smem() {
@@ -768,9 +842,10 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
                      const pccp_solve_opts* opts, pccp_result* results, void* stream) {
   if (!models || n_models < 0 || !opts || !results) return PCCP_ERR_INVALID;
   if (n_models == 0) return PCCP_OK;
-  if (opts->strategy != PCCP_INPUT_ORDER && opts->strategy != PCCP_FIRST_FAIL)
-    return PCCP_ERR_INVALID;
-  if (opts->mode != PCCP_OPTIMISE && opts->mode != PCCP_COUNT_ALL) return PCCP_ERR_INVALID;
+  {
+    const int rc0 = check_strategy(opts);
+    if (rc0 != PCCP_OK) return rc0;
+  }
   const int smem_max = max_dyn_smem();
   const int sms = sm_count();
   if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
@@ -801,10 +876,11 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     max_tw = std::max(max_tw, track_words(m->n_vars, m->n_lin));
   }
   bool global = false;
-  const size_t smem = plan_solve_smem(max_img, max_tw, max_vars, smem_max, &global);
+  const int xw = policy_x_words(opts, max_branch);
+  const size_t smem = plan_solve_smem(max_img, max_tw, max_vars, smem_max, &global, xw);
   if (smem > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   if (global && opts->threads <= 0) threads = 1024;
-  const auto ksolve = opts->skip_stable ? k_solve<true> : k_solve<false>;
+  const auto ksolve = solve_kernel(opts);
   PCCP_CUDA(cudaFuncSetAttribute(ksolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
   int per_sm = 0;
@@ -855,6 +931,9 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     a.max_image_bytes = global ? 0 : max_img;
     a.max_track_words = max_tw;
     a.table_global = global ? 1 : 0;
+    a.x_words = xw;
+    a.max_vars_smem = max_vars;
+    a.policy = opts->strategy == PCCP_LEARNED ? policy_dev(opts->policy) : nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
       rc = PCCP_ERR_CUDA;
       break;
@@ -920,8 +999,10 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
   int team = o->threads > 0 ? o->threads : 128;
   if (team % 32 != 0 || team > 1024) return PCCP_ERR_INVALID;
+  const int xw = policy_x_words(o, m->n_branch);
   const size_t per_team = sizeof(EpsCtrl) + 4 * ((track_words(m->n_vars, m->n_lin) + 3) & ~3) +
-                          static_cast<size_t>(m->n_vars) * sizeof(int2);
+                          static_cast<size_t>(m->n_vars) * sizeof(int2) +
+                          4 * static_cast<size_t>(xw);
   const bool global = static_cast<size_t>(m->image_bytes) + 16 + per_team >
                       static_cast<size_t>(smem_max);
   const size_t base = (global ? 0 : static_cast<size_t>(m->image_bytes)) + 16;
@@ -930,8 +1011,11 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   const int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
   const int teams = std::max(1, std::min({8, fit, 1024 / team}));
   const size_t smem = base + static_cast<size_t>(teams) * per_team;
-  const auto kexp = o->skip_stable ? k_eps_expand<true> : k_eps_expand<false>;
-  const auto ksol = o->skip_stable ? k_eps_solve<true> : k_eps_solve<false>;
+  const bool learned = o->strategy == PCCP_LEARNED;
+  const auto kexp = learned ? k_eps_expand<false, true>
+                            : (o->skip_stable ? k_eps_expand<true, false> : k_eps_expand<false, false>);
+  const auto ksol = learned ? k_eps_solve<false, true>
+                            : (o->skip_stable ? k_eps_solve<true, false> : k_eps_solve<false, false>);
   PCCP_CUDA(cudaFuncSetAttribute(kexp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
   PCCP_CUDA(cudaFuncSetAttribute(ksol, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -998,6 +1082,8 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     a.obj_ub = o->obj_ub;
     a.track_words = track_words(m->n_vars, m->n_lin);
     a.table_global = global ? 1 : 0;
+    a.x_words = xw;
+    a.policy = o->strategy == PCCP_LEARNED ? policy_dev(o->policy) : nullptr;
     a.node_limit = o->node_limit;
     a.time_limit_ns = o->time_limit_ms > 0 ? o->time_limit_ms * 1000000ll : 0;
     uint8_t* lin = d + o_la;
@@ -1113,9 +1199,10 @@ extern "C" {
 int pccp_solve(const pccp_model* m, const pccp_solve_opts* opts, pccp_result* result,
                void* stream) {
   if (!m || !opts || !result) return PCCP_ERR_INVALID;
-  if (opts->strategy != PCCP_INPUT_ORDER && opts->strategy != PCCP_FIRST_FAIL)
-    return PCCP_ERR_INVALID;
-  if (opts->mode != PCCP_OPTIMISE && opts->mode != PCCP_COUNT_ALL) return PCCP_ERR_INVALID;
+  {
+    const int rc0 = check_strategy(opts);
+    if (rc0 != PCCP_OK) return rc0;
+  }
   if (!opts->deterministic) {
     const int rc = check_device(m);
     if (rc != PCCP_OK) return rc;
@@ -1131,3 +1218,4 @@ int pccp_solve(const pccp_model* m, const pccp_solve_opts* opts, pccp_result* re
 
 #include "pccp_noalloc.inc"
 #include "pccp_batch.inc"
+#include "pccp_policy.inc"

@@ -25,7 +25,7 @@ enum : int { kFixpoint = 0, kFailed = 1, kError = 2 };
 struct TableHeader {
   int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective, image_bytes;
   int32_t off_t, off_rf, off_lin, off_terms, off_branch, n_lin_long, off_lin_long, off_terms_long;
-  int32_t off_adj_off, off_adj, n_adj, pad[5];
+  int32_t off_adj_off, off_adj, n_adj, off_bstat, pad[4];
 };
 static_assert(sizeof(TableHeader) == 96, "header must be 96 bytes");
 
@@ -51,6 +51,7 @@ struct Tab {
   const int32_t* branch;
   const int32_t* adj_off;   // [n_vars + 1]: linear rows holding each variable
   const int32_t* adj;       // row ids: short rows 0.., long rows n_lin..
+  const float* bstat;       // [n_branch][8] static features of the branch variables
   int n_vars, n_t, n_rf, n_lin, n_lin_long, n_terms, n_branch, objective;
 };
 
@@ -74,6 +75,7 @@ __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
   tb.branch = reinterpret_cast<const int32_t*>(img + h->off_branch);
   tb.adj_off = reinterpret_cast<const int32_t*>(img + h->off_adj_off);
   tb.adj = reinterpret_cast<const int32_t*>(img + h->off_adj);
+  tb.bstat = reinterpret_cast<const float*>(img + h->off_bstat);
   return tb;
 }
 

@@ -56,14 +56,14 @@ __device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4],
 }
 
 // The 12 features of branch variable number k (index into the branch list)
-// at a node, written as 16 bf16 (4 zero pads) into row k of X (8 words/row).
+// at a node, written as 16 bf16 (4 zero pads) into `row` (8 words).
 //   0 (lb - lb0) / (w0 + 1)     1 (ub - lb0) / (w0 + 1)    2 (ub - lb) / (w0 + 1)
 //   3 log2(1 + ub - lb) / 16    4 out-degree / 8           5 summed offsets / (w0 + 1)
 //   6 in-degree / 8             7 reified rows / 64         8 linear rows / 16
 //   9 k / n_branch              10 depth / (depth + 32)    11 objective progress
 // (w0 = root width of the variable; objective progress = (lb(obj) - lb0(obj))
 // / (root width of obj + 1), 0 without an objective.)
-__device__ __forceinline__ void write_features(uint32_t* X, int k, int v, int2 D, int2 R,
+__device__ __forceinline__ void write_features(uint32_t* row, int k, int2 D, int2 R,
                                                const BranchStatic& s, int n_branch, int depth,
                                                float obj_prog) {
   const float inv = 1.0f / (static_cast<float>(R.y - R.x) + 1.0f);
@@ -78,7 +78,6 @@ __device__ __forceinline__ void write_features(uint32_t* X, int k, int v, int2 D
   const float f8 = s.n_linear * (1.0f / 16.0f);
   const float f9 = static_cast<float>(k) / static_cast<float>(n_branch);
   const float f10 = static_cast<float>(depth) / (static_cast<float>(depth) + 32.0f);
-  uint32_t* row = X + 8 * k;
   row[0] = pack_bf16x2(f0, f1);
   row[1] = pack_bf16x2(f2, f3);
   row[2] = pack_bf16x2(f4, f5);
@@ -87,7 +86,6 @@ __device__ __forceinline__ void write_features(uint32_t* X, int k, int v, int2 D
   row[5] = pack_bf16x2(f10, obj_prog);
   row[6] = 0u;
   row[7] = 0u;
-  (void)v;
 }
 
 // Scores of rows 16c .. 16c+15 of X by one warp.  On return the lanes with
@@ -147,6 +145,50 @@ __device__ __forceinline__ uint32_t score_key(float s) {
 __device__ __forceinline__ unsigned long long learned_key(float s, int k) {
   return (static_cast<unsigned long long>(score_key(s)) << 32) |
          static_cast<unsigned long long>(0xffffffffu - static_cast<uint32_t>(k));
+}
+
+// Learned selection by a whole team after a fixed point: features of every
+// branch variable into X (shared memory, 8 words per row, rows padded to a
+// multiple of 16), a team barrier, then warps score 16-row chunks and submit
+// the unfixed candidates' keys to *sel in the minimum form of the plain
+// strategies (~learned_key: its low 32 bits are the branch index).
+__device__ __forceinline__ void learned_select(const Tab& tb, int2* st,
+                                               const int2* __restrict__ root, const Team& tm,
+                                               const PolicyDev* __restrict__ pol, uint32_t* X,
+                                               unsigned long long* sel, int depth) {
+  const int nb = tb.n_branch, nbp = (nb + 15) & ~15;
+  const BranchStatic* bs = reinterpret_cast<const BranchStatic*>(tb.bstat);
+  float prog = 0.f;
+  if (tb.objective >= 0) {
+    const int2 RO = __ldg(root + tb.objective);
+    prog = static_cast<float>(ld_dom(st, tb.objective).x - RO.x) /
+           (static_cast<float>(RO.y - RO.x) + 1.f);
+  }
+  for (int k = tm.tid; k < nbp; k += tm.nthr) {
+    if (k < nb) {
+      const int v = tb.branch[k];
+      write_features(X + 8 * k, k, ld_dom(st, v), __ldg(root + v), bs[k], nb, depth, prog);
+    } else {
+      for (int w = 0; w < 8; ++w) X[8 * k + w] = 0u;
+    }
+  }
+  team_bar(tm.bar, tm.nthr);
+  for (int c = tm.warp; c < nbp / 16; c += tm.nwarps) {
+    float lo, hi;
+    mlp_score_chunk(pol, X, c, &lo, &hi);
+    if ((tm.lane & 3) == 0) {
+      const int r0 = 16 * c + (tm.lane >> 2);
+      const int r1 = r0 + 8;
+      if (r0 < nb) {
+        const int2 D = ld_dom(st, tb.branch[r0]);
+        if (D.x < D.y) atomicMin(sel, ~learned_key(lo, r0));
+      }
+      if (r1 < nb) {
+        const int2 D = ld_dom(st, tb.branch[r1]);
+        if (D.x < D.y) atomicMin(sel, ~learned_key(hi, r1));
+      }
+    }
+  }
 }
 
 }  // namespace pccp

@@ -1,0 +1,132 @@
+"""Learned branching: data from the solver's own propagation, training on the
+library's tensor-core kernels, and the policy as a search strategy.
+
+Data.  Search nodes are random descents of a model's tree (input-order
+branching decisions), propagated to their fixed points by pccp_propagate.
+At each node with at least two unfixed branch variables every candidate is
+probed the way strong branching does: both children of its lower-half split
+are propagated (again by pccp_propagate, all children of a batch in one
+launch) and scored by the failures they expose and the domain reduction they
+cause.  The target of a node is the softmax of these scores over its
+candidates; the policy learns to rank candidates like the probe without
+running it.  Features come from pccp_policy_features, i.e. exactly the values
+the search kernels feed the network.
+
+Training.  pccp_policy_train_step: forward, listwise softmax cross-entropy,
+backward and Adam, with every matrix product on the tensor cores (BF16
+operands, FP32 accumulation).
+"""
+import numpy as np
+
+from . import Model, Policy, propagate, policy_features, rcpsp
+from . import PCCP_FIXPOINT
+
+PROBE_TEMPERATURE = 0.05
+
+
+def _device():
+    import torch
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def collect(instances, nodes_per_model=256, seed=0, max_decisions=15):
+    """Training groups from a list of scheduling instances.  Returns a dict of
+    CUDA tensors: features [R, 12], group_off [G + 1], target [R]."""
+    import torch
+    from synthetic import draw_partial_assignments
+    dev = _device()
+    feats, targets, sizes = [], [], []
+    for mi, inst in enumerate(instances):
+        rows = rcpsp.build_rows(inst)
+        model = Model.from_rows(rows)
+        nodes = draw_partial_assignments(inst.n, inst.horizon, nodes_per_model,
+                                         seed=seed * 100_003 + mi, max_decisions=max_decisions)
+        lb_h, ub_h = rcpsp.node_stores(rows, nodes)
+        lb = torch.from_numpy(lb_h).to(dev)
+        ub = torch.from_numpy(ub_h).to(dev)
+        st, _ = propagate(model, lb, ub)
+        ok = (st == PCCP_FIXPOINT).nonzero().flatten()
+        if ok.numel() == 0:
+            continue
+        lb, ub = lb[ok].contiguous(), ub[ok].contiguous()
+        depth = torch.tensor([len(nodes[i]) for i in ok.tolist()], dtype=torch.int32, device=dev)
+        branch = torch.from_numpy(model.branch.astype(np.int64)).to(dev)
+        blb, bub = lb[:, branch], ub[:, branch]
+        unfixed = blb < bub                                    # [N, nb]
+        keep = unfixed.sum(dim=1) >= 2
+        if keep.sum() == 0:
+            continue
+        lb, ub, depth = lb[keep].contiguous(), ub[keep].contiguous(), depth[keep].contiguous()
+        blb, bub, unfixed = blb[keep], bub[keep], unfixed[keep]
+        f = policy_features(model, lb, ub, depth)             # [N, nb, 12]
+        node_idx, cand = unfixed.nonzero(as_tuple=True)        # candidates
+        var = branch[cand]
+        mid = blb[node_idx, cand] + (bub[node_idx, cand] - blb[node_idx, cand]) // 2
+        # children: left ub(var) <= mid, right lb(var) >= mid + 1
+        clb = torch.cat([lb[node_idx], lb[node_idx]]).clone()
+        cub = torch.cat([ub[node_idx], ub[node_idx]]).clone()
+        c = node_idx.numel()
+        ar = torch.arange(c, device=dev)
+        cub[ar, var] = torch.minimum(cub[ar, var], mid.to(torch.int32))
+        clb[c + ar, var] = torch.maximum(clb[c + ar, var], (mid + 1).to(torch.int32))
+        clb, cub = clb.contiguous(), cub.contiguous()
+        cst, _ = propagate(model, clb, cub)
+        failed = (cst != PCCP_FIXPOINT).float()
+        w_before = (bub - blb).float().sum(dim=1)[node_idx].clamp(min=1.0)
+        w_after = (cub[:, branch] - clb[:, branch]).float().sum(dim=1)
+        red = ((w_before.repeat(2) - w_after) / w_before.repeat(2)) * (1 - failed)
+        score = (failed[:c] + failed[c:]) * 2.0 + red[:c] + red[c:]
+        # groups: one per node, candidates in row-major order of (node, branch index)
+        counts = torch.bincount(node_idx, minlength=lb.shape[0])
+        target = torch.empty_like(score)
+        off = 0
+        for cnt in counts.tolist():
+            s = score[off:off + cnt] / PROBE_TEMPERATURE
+            target[off:off + cnt] = torch.softmax(s, dim=0)
+            off += cnt
+        feats.append(f[node_idx, cand])
+        targets.append(target)
+        sizes.append(counts[counts > 0])
+    features = torch.cat(feats).contiguous()
+    target = torch.cat(targets).contiguous()
+    sizes = torch.cat(sizes)
+    group_off = torch.zeros(sizes.numel() + 1, dtype=torch.int32, device=dev)
+    group_off[1:] = torch.cumsum(sizes, 0).to(torch.int32)
+    return {"features": features, "group_off": group_off, "target": target}
+
+
+def batches(data, groups_per_batch, seed):
+    """Random mini-batches of whole groups (features, group_off, target)."""
+    import torch
+    g = np.random.default_rng(seed)
+    off = data["group_off"].cpu().numpy()
+    n_groups = off.size - 1
+    order = g.permutation(n_groups)
+    for b in range(0, n_groups, groups_per_batch):
+        sel = np.sort(order[b:b + groups_per_batch])
+        idx = np.concatenate([np.arange(off[i], off[i + 1]) for i in sel])
+        sizes = off[sel + 1] - off[sel]
+        go = np.zeros(sel.size + 1, dtype=np.int32)
+        go[1:] = np.cumsum(sizes)
+        it = torch.from_numpy(idx).to(data["features"].device)
+        yield (data["features"][it].contiguous(), torch.from_numpy(go).to(it.device),
+               data["target"][it].contiguous())
+
+
+def train(policy: Policy, data, epochs=4, groups_per_batch=256, lr=2e-3, seed=0):
+    """Adam epochs over the data; returns the mean loss of every epoch."""
+    losses = []
+    for e in range(epochs):
+        ls = [policy.train_step(f, go, t, lr=lr) for f, go, t in
+              batches(data, groups_per_batch, seed + e)]
+        losses.append(float(np.mean(ls)))
+    return losses
+
+
+def ranking_accuracy(policy: Policy, data):
+    """Fraction of groups whose highest-scoring candidate is the target's."""
+    s = policy.score(data["features"]).cpu().numpy()
+    t = data["target"].cpu().numpy()
+    off = data["group_off"].cpu().numpy()
+    hits = [int(np.argmax(s[a:b]) == np.argmax(t[a:b])) for a, b in zip(off[:-1], off[1:])]
+    return float(np.mean(hits))
