@@ -521,7 +521,20 @@ def run_learned(args):
     both = [(a, b) for a, b in zip(out["first_fail"]["best_makespans"],
                                    out["learned"]["best_makespans"])
             if a is not None and b is not None]
+    # 8-task models: complete searches, so nodes and time to proven optimum
+    tiny = [pccp.Model.from_rcpsp(config_instance("tiny8", s)) for s in range(100)]
+    proofs = {}
+    for name, kw in (("first_fail", {"strategy": pccp.PCCP_FIRST_FAIL}),
+                     ("learned", {"strategy": pccp.PCCP_LEARNED, "policy": pol})):
+        res = pccp.solve_batch(tiny, **kw)
+        proofs[name] = {"kernel_ms": res[0]["elapsed_ms"],
+                        "nodes_total": sum(r["nodes"] for r in res),
+                        "proven": sum(r["status"] == pccp.PCCP_RES_OPTIMAL for r in res),
+                        "optima": [r["objective"] for r in res]}
+    assert proofs["first_fail"]["optima"] == proofs["learned"]["optima"], "optima must agree"
     line = {"metric": "time and nodes to proven optimum, learned vs first-fail",
+            "proofs_tiny8": {k: {kk: vv for kk, vv in v.items() if kk != "optima"}
+                             for k, v in proofs.items()},
             "workload": f"64 seeded 60-task 4-resource models, one launch per strategy, "
                         f"{args.learned_nodes} nodes and {args.learned_ms} ms per model",
             "training": {"groups": int(data["group_off"].numel() - 1),
@@ -532,6 +545,36 @@ def run_learned(args):
             "learned": {k: v for k, v in out["learned"].items() if k != "best_makespans"},
             "learned_better_equal_worse": [sum(b < a for a, b in both), sum(b == a for a, b in both),
                                            sum(b > a for a, b in both)]}
+    print(json.dumps(line), flush=True)
+
+
+def run_large(args):
+    """120-task models (14,521 variables, ~570 KB table read from global
+    memory) solved in one persistent launch, one 1024-thread team per model,
+    each model stopped after --large-ms; reports nodes/s, the bytes the row
+    evaluations read per second and the best makespans found."""
+    import torch
+    import paper_2207_12116_gb300 as pccp
+    torch.cuda.set_device(0)
+    models = [pccp.Model.from_rcpsp(config_instance("j120", 2000 + s))
+              for s in range(args.large_models)]
+    bytes_per_row = models[0].info.bytes_per_sweep / models[0].rows
+    strategy = pccp.PCCP_FIRST_FAIL
+    t0 = time.perf_counter()
+    res = pccp.solve_batch(models, strategy=strategy, time_limit_ms=args.large_ms)
+    wall = time.perf_counter() - t0
+    ms = res[0]["elapsed_ms"]
+    nodes = sum(r["nodes"] for r in res)
+    rows = sum(r["rows_evaluated"] for r in res)
+    found = [r["objective"] for r in res if r["has_solution"]]
+    line = {"metric": "search nodes/s, best makespan under a time limit (120-task models)",
+            "workload": f"{args.large_models} seeded 120-task 4-resource models, first-fail, "
+                        f"one launch, {args.large_ms} ms per model",
+            "nodes_per_s": nodes / (ms / 1000), "propagator_evals_per_s": rows / (ms / 1000),
+            "row_bytes_per_s": rows * bytes_per_row / (ms / 1000),
+            "kernel_ms": ms, "wall_s": wall, "nodes": nodes,
+            "models_with_solution": len(found),
+            "mean_best_makespan": float(np.mean(found)) if found else None}
     print(json.dumps(line), flush=True)
 
 
@@ -549,6 +592,10 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=8)
     ap.add_argument("--learned-nodes", type=int, default=20000)
     ap.add_argument("--learned-ms", type=int, default=20000)
+    ap.add_argument("--large", action="store_true",
+                    help="120-task models in one launch (own JSON line)")
+    ap.add_argument("--large-models", type=int, default=1024)
+    ap.add_argument("--large-ms", type=int, default=7000)
     ap.add_argument("--search-only", action="store_true",
                     help="small search leg only (64 models x 500 nodes; parallel runs "
                          "stopped after 2,000,000 nodes)")
@@ -564,6 +611,8 @@ def main():
         run_search_only(args)
     elif args.learned:
         run_learned(args)
+    elif args.large:
+        run_large(args)
     else:
         run_gpu(args)
 

@@ -7,10 +7,13 @@ At each node with at least two unfixed branch variables every candidate is
 probed the way strong branching does: both children of its lower-half split
 are propagated (again by pccp_propagate, all children of a batch in one
 launch) and scored by the failures they expose and the domain reduction they
-cause.  The target of a node is the softmax of these scores over its
-candidates; the policy learns to rank candidates like the probe without
-running it.  Features come from pccp_policy_features, i.e. exactly the values
-the search kernels feed the network.
+cause.  The expert blends this probe with first-fail's preference for small
+domains (a probe alone favours splits that fail or shrink domains, which
+makes depth-first dives thrash before any assignment completes); the target
+of a node is the softmax of the expert's scores over its candidates, and the
+policy learns to rank candidates like the expert without running the probe.
+Features come from pccp_policy_features, i.e. exactly the values the search
+kernels feed the network.
 
 Training.  pccp_policy_train_step: forward, listwise softmax cross-entropy,
 backward and Adam, with every matrix product on the tensor cores (BF16
@@ -22,6 +25,7 @@ from . import Model, Policy, propagate, policy_features, rcpsp
 from . import PCCP_FIXPOINT
 
 PROBE_TEMPERATURE = 0.05
+WIDTH_WEIGHT = 0.5  # expert score -= WIDTH_WEIGHT * log2(1 + domain width)
 
 
 def _device():
@@ -75,7 +79,9 @@ def collect(instances, nodes_per_model=256, seed=0, max_decisions=15):
         w_before = (bub - blb).float().sum(dim=1)[node_idx].clamp(min=1.0)
         w_after = (cub[:, branch] - clb[:, branch]).float().sum(dim=1)
         red = ((w_before.repeat(2) - w_after) / w_before.repeat(2)) * (1 - failed)
-        score = (failed[:c] + failed[c:]) * 2.0 + red[:c] + red[c:]
+        width = (bub[node_idx, cand] - blb[node_idx, cand]).float()
+        score = (failed[:c] + failed[c:]) * 2.0 + red[:c] + red[c:] \
+            - WIDTH_WEIGHT * torch.log2(1.0 + width)
         # groups: one per node, candidates in row-major order of (node, branch index)
         counts = torch.bincount(node_idx, minlength=lb.shape[0])
         target = torch.empty_like(score)
