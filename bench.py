@@ -466,6 +466,13 @@ def run_gpu(args):
             "wall_s_timed_loop": wall,
             "kernel_ms_min": min(kernel_ms), "kernel_ms_max": max(kernel_ms),
         }
+        if not args.no_probes:
+            # measured roofs (after the timed region): the nominal 128 B/clk/SM
+            # cross-checked by a conflict-free shared-load probe
+            probes = pccp.roofline_probes()
+            line["roofline"]["probes"] = probes
+            meas = probes["smem_load"]["per_clk_per_sm"] * sms * (sm_mhz or 0) * 1e6 / 1e9
+            line["roofline"]["frac_of_probe"] = achieved / meas if meas else None
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(inst, nodes)
         if not args.no_search:
@@ -558,7 +565,12 @@ def run_large(args):
     torch.cuda.set_device(0)
     models = [pccp.Model.from_rcpsp(config_instance("j120", 2000 + s))
               for s in range(args.large_models)]
-    bytes_per_row = models[0].info.bytes_per_sweep / models[0].rows
+    info = models[0].info
+    bytes_per_row = info.bytes_per_sweep / models[0].rows
+    # the table's share of those bytes (rows and terms, read from global
+    # memory through L1/L2 at this size): T 12 B, Rf 16 B, L 12 B + 8 B/term
+    table_per_row = (12 * info.n_temporal + 16 * info.n_reified + 12 * info.n_linear
+                     + 8 * info.n_terms) / models[0].rows
     strategy = pccp.PCCP_FIRST_FAIL
     t0 = time.perf_counter()
     res = pccp.solve_batch(models, strategy=strategy, time_limit_ms=args.large_ms)
@@ -575,6 +587,11 @@ def run_large(args):
             "kernel_ms": ms, "wall_s": wall, "nodes": nodes,
             "models_with_solution": len(found),
             "mean_best_makespan": float(np.mean(found)) if found else None}
+    tbs = rows * table_per_row / (ms / 1000) / 1e9
+    line["table_stream"] = {"achieved_gbs": tbs, "table_bytes": info.table_bytes}
+    if not args.no_probes:
+        l2 = pccp.roofline_probes()["l2_read"]
+        line["table_stream"].update({"l2_probe_gbs": l2["gbs"], "frac_of_l2_probe": tbs / l2["gbs"]})
     print(json.dumps(line), flush=True)
 
 
@@ -592,6 +609,8 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=8)
     ap.add_argument("--learned-nodes", type=int, default=20000)
     ap.add_argument("--learned-ms", type=int, default=20000)
+    ap.add_argument("--no-probes", action="store_true",
+                    help="skip the roofline microbenchmarks after the timed region")
     ap.add_argument("--large", action="store_true",
                     help="120-task models in one launch (own JSON line)")
     ap.add_argument("--large-models", type=int, default=1024)

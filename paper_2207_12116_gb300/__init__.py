@@ -30,7 +30,7 @@ __all__ = ["Model", "pccp_model_create", "pccp_model_destroy", "pccp_model_get_i
            "pccp_policy_create", "pccp_policy_destroy", "pccp_policy_get_weights",
            "pccp_policy_features", "pccp_policy_score", "pccp_policy_train_step",
            "pccp_error_string", "propagate", "propagate_host", "solve", "solve_batch",
-           "PccpError", "load", "library_path"]
+           "PccpError", "load", "library_path", "pccp_probe", "roofline_probes"]
 
 
 def _i32(a, shape=None):
@@ -112,6 +112,31 @@ def pccp_batch_destroy(handle):
 
 def pccp_error_string(code):
     return _abi.error_string(code)
+
+
+def pccp_probe(kind, iters=0):
+    """One roofline microbenchmark (include/pccp_probe.h) on the current
+    device: {"work", "ms", "sm_cycles", "n_sms", "ctas"}."""
+    r = _abi.pccp_probe_result()
+    check(_abi.load_probe().pccp_probe(kind, iters, ctypes.byref(r)), "pccp_probe")
+    return {"work": r.work, "ms": r.ms, "sm_cycles": r.sm_cycles, "n_sms": r.n_sms,
+            "ctas": r.ctas}
+
+
+def roofline_probes():
+    """The measured roofs: shared-memory load bytes and relaxed shared atomics
+    per clock per SM, scattered 8-byte interval loads per clock per SM, and L2
+    read GB/s; each with the SM clock the probe ran at."""
+    out = {}
+    for name, kind, unit in (("smem_load", _abi.PCCP_PROBE_SMEM_LOAD, "B/clk/SM"),
+                             ("smem_atomic", _abi.PCCP_PROBE_SMEM_ATOM, "ops/clk/SM"),
+                             ("smem_scattered_v2", _abi.PCCP_PROBE_SMEM_DOM, "B/clk/SM")):
+        r = pccp_probe(kind)
+        out[name] = {"per_clk_per_sm": r["work"] / (r["sm_cycles"] * r["n_sms"]), "unit": unit,
+                     "sm_mhz": r["sm_cycles"] / (r["ms"] * 1e3)}
+    r = pccp_probe(_abi.PCCP_PROBE_L2_READ)
+    out["l2_read"] = {"gbs": r["work"] / (r["ms"] * 1e6), "sm_mhz": r["sm_cycles"] / (r["ms"] * 1e3)}
+    return out
 
 
 # ------------------------------------------------------------------- model

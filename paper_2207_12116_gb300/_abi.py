@@ -97,6 +97,19 @@ SIGNATURES = {
 }
 
 
+class pccp_probe_result(ctypes.Structure):
+    _fields_ = [("work", ctypes.c_double), ("ms", ctypes.c_double), ("sm_cycles", ctypes.c_double),
+                ("n_sms", I32), ("ctas", I32)]
+
+
+# every entry point declared in include/pccp_probe.h
+PROBE_SIGNATURES = {
+    "pccp_probe": (ctypes.c_int, [I32, I32, ctypes.POINTER(pccp_probe_result)]),
+}
+PCCP_PROBE_SMEM_LOAD, PCCP_PROBE_SMEM_ATOM, PCCP_PROBE_SMEM_DOM, PCCP_PROBE_L2_READ = 0, 1, 2, 3
+_probe_lib = None
+
+
 class PccpError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
@@ -124,6 +137,25 @@ def load(build_if_missing: bool = True):
                 fn.argtypes = args
             _lib = lib
     return _lib
+
+
+def load_probe(build_if_missing: bool = True):
+    """Load libpccp_probe.so, the roofline microbenchmarks."""
+    global _probe_lib
+    with _lock:
+        if _probe_lib is None:
+            path = _build.PROBE_LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise ImportError(f"probe library not built: {path}")
+                _build.build()
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in PROBE_SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _probe_lib = lib
+    return _probe_lib
 
 
 def error_string(code: int) -> str:

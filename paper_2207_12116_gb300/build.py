@@ -1,8 +1,10 @@
-"""In-tree build of the CUDA library libpccp.so for sm_103a (nvcc, no cmake).
+"""In-tree build of the CUDA libraries for sm_103a (nvcc, no cmake).
 
-The library is the product: the Python binding loads it and nothing else
-computes the method.  Built artefacts go to paper_2207_12116_gb300/_build/
-(git-ignored)."""
+libpccp.so is the product: the Python binding loads it and nothing else
+computes the method.  libpccp_probe.so holds the roofline microbenchmarks
+(include/pccp_probe.h).  Built artefacts go to paper_2207_12116_gb300/_build/
+(git-ignored); the two libraries compile in parallel."""
+import glob
 import os
 import subprocess
 
@@ -11,12 +13,15 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpccp.so")
+PROBE_LIB = os.path.join(BUILD, "libpccp_probe.so")
 SOURCES = [os.path.join(CSRC, "pccp.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "pccp_device.cuh"), os.path.join(CSRC, "k_propagate.cuh"),
-                  os.path.join(CSRC, "pccp_noalloc.inc"),
-                  os.path.join(CSRC, "pccp_batch.inc"), os.path.join(CSRC, "k_solve_eps.cuh"),
-                  os.path.join(ROOT, "include", "pccp.h")]
+PROBE_SOURCES = [os.path.join(CSRC, "roofline_probe.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def deps():
+    return (glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            glob.glob(os.path.join(CSRC, "*.inc")) + glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def nvcc() -> str:
@@ -26,22 +31,32 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(p) > t for p in DEPS)
+    t = os.path.getmtime(lib)
+    return any(os.path.getmtime(p) > t for p in deps())
+
+
+def _command(sources, out, verbose):
+    return [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+            "-Xptxas", "-v" if verbose else "-O3", *sources, "-o", out]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile whichever library is missing or older than a source; returns
+    the path of libpccp.so."""
     os.makedirs(BUILD, exist_ok=True)
-    if not force and not stale():
-        return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-Xptxas", "-v" if verbose else "-O3", *SOURCES, "-o", tmp]
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    jobs = []
+    for sources, lib in ((SOURCES, LIB), (PROBE_SOURCES, PROBE_LIB)):
+        if force or stale(lib):
+            tmp = lib + f".{os.getpid()}.tmp"
+            jobs.append((subprocess.Popen(_command(sources, tmp, verbose)), tmp, lib))
+    failed = [lib for proc, _, lib in jobs if proc.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, f"nvcc for {', '.join(failed)}")
+    for _, tmp, lib in jobs:
+        os.replace(tmp, lib)
     return LIB
 
 

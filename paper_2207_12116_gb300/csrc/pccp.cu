@@ -21,6 +21,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/pccp.h"
@@ -410,6 +411,31 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   // conflicts).  Row order never changes the fixed point (Sec. 3).
   std::stable_sort(RF.begin(), RF.end(),
                    [](const uint2& p, const uint2& q) { return (p.y & 0xffffu) < (q.y & 0xffffu); });
+  // Rows over the same two variables with the roles swapped are evaluated
+  // together (one load of x and y for both); the rest stay single.
+  std::vector<uint4> RFP;
+  {
+    std::vector<uint2> single;
+    std::unordered_map<uint32_t, std::vector<size_t>> waiting;  // (x | y << 16) -> rows
+    std::vector<char> used(RF.size(), 0);
+    for (size_t r = 0; r < RF.size(); ++r) waiting[RF[r].x].push_back(r);
+    for (size_t r = 0; r < RF.size(); ++r) {
+      if (used[r]) continue;
+      const uint32_t x = RF[r].x & 0xffffu, y = RF[r].x >> 16;
+      if (x == y) continue;
+      auto it = waiting.find(y | (x << 16));
+      if (it == waiting.end()) continue;
+      for (size_t q : it->second) {
+        if (used[q] || q == r) continue;
+        used[r] = used[q] = 1;
+        RFP.push_back(make_uint4(RF[r].x, RF[r].y, RF[q].y, 0u));
+        break;
+      }
+    }
+    for (size_t r = 0; r < RF.size(); ++r)
+      if (!used[r]) single.push_back(RF[r]);
+    RF.swap(single);
+  }
   if (d->n_linear > 0 && d->linear_off[0] != 0) return PCCP_ERR_INVALID;
   for (int32_t i = 0; i < d->n_linear; ++i) {
     const int32_t o0 = d->linear_off[i], o1 = d->linear_off[i + 1];
@@ -453,8 +479,10 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
       const LinRow& row = short_rows[r];
       const size_t lane = r - t0;
       for (size_t k = 0; k < row.terms.size(); ++k) TERMS[tile + 32 * k + lane] = row.terms[k];
+      bool pos = true;  // flag 1: every coefficient positive
+      for (uint32_t t : row.terms) pos = pos && (static_cast<int32_t>(t) >> 16) > 0;
       L.push_back(make_int4(row.c, static_cast<int32_t>(tile + lane),
-                            static_cast<int32_t>(row.terms.size()), 0));
+                            static_cast<int32_t>(row.terms.size()), pos ? 1 : 0));
     }
   }
   for (const LinRow& row : long_rows) {
@@ -511,16 +539,22 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   h.n_vars = static_cast<int32_t>(nv);
   h.n_t = static_cast<int32_t>(T.size());
   h.n_rf = static_cast<int32_t>(RF.size());
+  h.n_rfp = static_cast<int32_t>(RFP.size());
   h.n_lin = static_cast<int32_t>(L.size());
   h.n_lin_long = static_cast<int32_t>(LL.size());
   h.n_terms = n_terms;
   h.n_branch = d->n_branch;
   h.objective = d->objective;
+  h.rows_sweep = h.n_t + h.n_rf + 2 * h.n_rfp + h.n_lin + h.n_lin_long;
+  if (bytes_per_sweep > static_cast<int64_t>(INT32_MAX)) return PCCP_ERR_UNSUPPORTED;
+  h.bytes_sweep = static_cast<int32_t>(bytes_per_sweep);
   size_t off = sizeof(TableHeader);
   h.off_t = static_cast<int32_t>(off);
   off = align16(off + T.size() * sizeof(uint2));
   h.off_rf = static_cast<int32_t>(off);
   off = align16(off + RF.size() * sizeof(uint2));
+  h.off_rfp = static_cast<int32_t>(off);
+  off = align16(off + RFP.size() * sizeof(uint4));
   h.off_lin = static_cast<int32_t>(off);
   off = align16(off + L.size() * sizeof(int4));
   h.off_terms = static_cast<int32_t>(off);
@@ -545,6 +579,8 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   std::memcpy(p->image.data(), &h, sizeof(h));
   if (!T.empty()) std::memcpy(p->image.data() + h.off_t, T.data(), T.size() * sizeof(uint2));
   if (!RF.empty()) std::memcpy(p->image.data() + h.off_rf, RF.data(), RF.size() * sizeof(uint2));
+  if (!RFP.empty())
+    std::memcpy(p->image.data() + h.off_rfp, RFP.data(), RFP.size() * sizeof(uint4));
   if (!L.empty()) std::memcpy(p->image.data() + h.off_lin, L.data(), L.size() * sizeof(int4));
   if (!TERMS.empty())
     std::memcpy(p->image.data() + h.off_terms, TERMS.data(), TERMS.size() * sizeof(uint32_t));
@@ -562,7 +598,7 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
     std::memcpy(p->image.data() + h.off_bstat, BST.data(), BST.size() * sizeof(BranchStatic));
   p->n_vars = h.n_vars;
   p->n_t = h.n_t;
-  p->n_rf = h.n_rf;
+  p->n_rf = h.n_rf + 2 * h.n_rfp;
   p->n_lin = h.n_lin + h.n_lin_long;
   p->n_terms = h.n_terms;
   p->n_branch = h.n_branch;
@@ -668,8 +704,10 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   if (global && !(cfg && cfg->team_threads > 0)) team = 1024;
   int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
-  // default: 4 teams of 128 threads per CTA, three CTAs per SM (48 warps)
-  int teams = (cfg && cfg->teams_per_cta > 0) ? cfg->teams_per_cta : 4;
+  // default: 8 teams of 128 threads per CTA, one CTA per SM (32 warps of up
+  // to 64 registers; measured ahead of 4 x 128 with three CTAs per SM and a
+  // 40-register cap)
+  int teams = (cfg && cfg->teams_per_cta > 0) ? cfg->teams_per_cta : 8;
   if (teams > kMaxTeamsPerCta) return PCCP_ERR_INVALID;
   teams = std::min({teams, fit, 1024 / team});
   if (cfg && cfg->teams_per_cta > 0 && teams < cfg->teams_per_cta) return PCCP_ERR_SMEM;

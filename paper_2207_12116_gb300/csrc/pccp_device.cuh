@@ -25,14 +25,16 @@ enum : int { kFixpoint = 0, kFailed = 1, kError = 2 };
 struct TableHeader {
   int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective, image_bytes;
   int32_t off_t, off_rf, off_lin, off_terms, off_branch, n_lin_long, off_lin_long, off_terms_long;
-  int32_t off_adj_off, off_adj, n_adj, off_bstat, pad[4];
+  int32_t off_adj_off, off_adj, n_adj, off_bstat, off_rfp, n_rfp;
+  int32_t rows_sweep;   // row evaluations in one full sweep (a reified pair counts 2)
+  int32_t bytes_sweep;  // their algorithmic bytes
 };
 static_assert(sizeof(TableHeader) == 96, "header must be 96 bytes");
 
 // Row encodings (structure of arrays, one array per row kind):
 //   temporal  uint2 {x | y << 16, d}              x + d <= y
 //   reified   uint2 {x | y << 16, b | d << 16}    b <=> (x <= y && y < x + d), d int16
-//   linear    int4  {c, base, len, 0}             sum coef*var <= c
+//   linear    int4  {c, base, len, flags}         sum coef*var <= c; flags: 1 all coef > 0
 //   term      uint32 var | coef << 16             coef int16
 // Linear rows of at most kShortRow terms are evaluated by one thread each and
 // stored in tiles of 32 rows, transposed: term t of the row in lane l of a
@@ -44,6 +46,7 @@ constexpr int kShortRow = 64;
 struct Tab {
   const uint2* t;
   const uint2* rf;
+  const uint4* rfp;         // reified pairs {x | y << 16, b1 | d1 << 16, b2 | d2 << 16, 0}
   const int4* lin;          // short rows
   const uint32_t* terms;    // their tiled terms
   const int4* lin_long;     // long rows
@@ -52,7 +55,8 @@ struct Tab {
   const int32_t* adj_off;   // [n_vars + 1]: linear rows holding each variable
   const int32_t* adj;       // row ids: short rows 0.., long rows n_lin..
   const float* bstat;       // [n_branch][8] static features of the branch variables
-  int n_vars, n_t, n_rf, n_lin, n_lin_long, n_terms, n_branch, objective;
+  int n_vars, n_t, n_rf, n_rfp, n_lin, n_lin_long, n_terms, n_branch, objective;
+  int rows_sweep, bytes_sweep;
 };
 
 __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
@@ -76,6 +80,10 @@ __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
   tb.adj_off = reinterpret_cast<const int32_t*>(img + h->off_adj_off);
   tb.adj = reinterpret_cast<const int32_t*>(img + h->off_adj);
   tb.bstat = reinterpret_cast<const float*>(img + h->off_bstat);
+  tb.n_rfp = h->n_rfp;
+  tb.rows_sweep = h->rows_sweep;
+  tb.bytes_sweep = h->bytes_sweep;
+  tb.rfp = reinterpret_cast<const uint4*>(img + h->off_rfp);
   return tb;
 }
 
@@ -281,9 +289,34 @@ __device__ __forceinline__ void eval_temporal(const Sweep& w, uint2 row, Flags& 
   }
 }
 
-// Reified row b <=> (A and B), A: x <= y, B: y <= x + d - 1: the four asks of
-// [[phi <=> psi]] (Sec. 2) evaluated on one snapshot; the candidates of every
-// ask are joined per bound with selects, and the tells (rare once the store
+// One reified row b <=> (A and B), A: x <= y, B: y <= x + d - 1, on a
+// snapshot X, Y, B: the four asks of [[phi <=> psi]] (Sec. 2) joined into the
+// candidate bounds (nlx .. nub start as the snapshot or earlier candidates).
+__device__ __forceinline__ void reified_rule(int2 X, int2 Y, int2 B, int d, int& nlx, int& nux,
+                                             int& nly, int& nuy, int& nlb, int& nub) {
+  const bool entA = X.y <= Y.x;           // ub x <= lb y
+  const bool entB = Y.y <= X.x + d - 1;   // ub y <= lb x + d - 1
+  const bool entNA = X.x >= Y.y + 1;      // lb x >= ub y + 1
+  const bool entNB = Y.x >= X.y + d;      // lb y >= ub x + d
+  if (B.x >= 1) {                         // b entailed: tell A and B
+    nux = min(nux, Y.y);
+    nly = max(nly, X.x);
+    nuy = min(nuy, X.y + d - 1);
+    nlx = max(nlx, Y.x - d + 1);
+  }
+  if (B.y <= 0 && entA) {                 // not b, A holds: tell not B (x + d <= y)
+    nly = max(nly, X.x + d);
+    nux = min(nux, Y.y - d);
+  }
+  if (B.y <= 0 && entB) {                 // not b, B holds: tell not A (y + 1 <= x)
+    nlx = max(nlx, Y.x + 1);
+    nuy = min(nuy, X.y - 1);
+  }
+  if (entA && entB) nlb = max(nlb, 1);    // A and B entailed: b
+  if (entNA || entNB) nub = min(nub, 0);  // not (A and B) entailed: not b
+}
+
+// Reified row, evaluated on one snapshot; the tells (rare once the store
 // settles) sit behind one branch.
 template <bool kTrack>
 __device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f) {
@@ -297,30 +330,8 @@ __device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f
   f.evals += 1;
   f.bytes += 40;
   const int2 X = ld_dom(w.st, x), Y = ld_dom(w.st, y), B = ld_dom(w.st, b);
-  const bool entA = X.y <= Y.x;           // ub x <= lb y
-  const bool entB = Y.y <= X.x + d - 1;   // ub y <= lb x + d - 1
-  const bool entNA = X.x >= Y.y + 1;      // lb x >= ub y + 1
-  const bool entNB = Y.x >= X.y + d;      // lb y >= ub x + d
-  const bool bt = B.x >= 1;               // b entailed: tell A and B
-  const bool bfA = B.y <= 0 && entA;      // not b, A holds: tell not B (x + d <= y)
-  const bool bfB = B.y <= 0 && entB;      // not b, B holds: tell not A (y + 1 <= x)
-  int nux = X.y, nlx = X.x, nuy = Y.y, nly = Y.x;
-  if (bt) {
-    nux = min(nux, Y.y);
-    nly = max(nly, X.x);
-    nuy = min(nuy, X.y + d - 1);
-    nlx = max(nlx, Y.x - d + 1);
-  }
-  if (bfA) {
-    nly = max(nly, X.x + d);
-    nux = min(nux, Y.y - d);
-  }
-  if (bfB) {
-    nlx = max(nlx, Y.x + 1);
-    nuy = min(nuy, X.y - 1);
-  }
-  const int nlb = (entA && entB) ? max(B.x, 1) : B.x;    // A and B entailed: b
-  const int nub = (entNA || entNB) ? min(B.y, 0) : B.y;  // not (A and B) entailed: not b
+  int nlx = X.x, nux = X.y, nly = Y.x, nuy = Y.y, nlb = B.x, nub = B.y;
+  reified_rule(X, Y, B, d, nlx, nux, nly, nuy, nlb, nub);
   if (nlx > X.x || nux < X.y || nly > Y.x || nuy < Y.y || nlb > B.x || nub < B.y) {
     tell_lb<kTrack>(w, x, nlx, X.x, X.y, f);
     tell_ub<kTrack>(w, x, nux, X.x, X.y, f);
@@ -328,6 +339,42 @@ __device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f
     tell_ub<kTrack>(w, y, nuy, Y.x, Y.y, f);
     tell_lb<kTrack>(w, b, nlb, B.x, B.y, f);
     tell_ub<kTrack>(w, b, nub, B.x, B.y, f);
+  }
+}
+
+// Two reified rows over the same pair of variables with the roles swapped,
+// b1 <=> (x <= y and y < x + d1) and b2 <=> (y <= x and x < y + d2) (the
+// overlap Booleans b_{i,j} and b_{j,i} of the scheduling model): both rules on
+// one snapshot, so x and y are loaded once for two rows.
+template <bool kTrack>
+__device__ __forceinline__ void eval_reified_pair(const Sweep& w, uint4 row, Flags& f) {
+  const int x = row.x & 0xffff, y = row.x >> 16;
+  const int b1 = row.y & 0xffff, d1 = static_cast<int>(row.y) >> 16;
+  const int b2 = row.z & 0xffff, d2 = static_cast<int>(row.z) >> 16;
+  if (kTrack && !w.full &&
+      !(test_bit(w.prev_chg, x) | test_bit(w.prev_chg, y) | test_bit(w.prev_chg, b1) |
+        test_bit(w.prev_chg, b2))) {
+    f.bytes += 32;  // row and four change words
+    return;
+  }
+  f.evals += 2;
+  f.bytes += 80;
+  const int2 X = ld_dom(w.st, x), Y = ld_dom(w.st, y);
+  const int2 B1 = ld_dom(w.st, b1), B2 = ld_dom(w.st, b2);
+  int nlx = X.x, nux = X.y, nly = Y.x, nuy = Y.y;
+  int nlb1 = B1.x, nub1 = B1.y, nlb2 = B2.x, nub2 = B2.y;
+  reified_rule(X, Y, B1, d1, nlx, nux, nly, nuy, nlb1, nub1);
+  reified_rule(Y, X, B2, d2, nly, nuy, nlx, nux, nlb2, nub2);
+  if (nlx > X.x || nux < X.y || nly > Y.x || nuy < Y.y || nlb1 > B1.x || nub1 < B1.y ||
+      nlb2 > B2.x || nub2 < B2.y) {
+    tell_lb<kTrack>(w, x, nlx, X.x, X.y, f);
+    tell_ub<kTrack>(w, x, nux, X.x, X.y, f);
+    tell_lb<kTrack>(w, y, nly, Y.x, Y.y, f);
+    tell_ub<kTrack>(w, y, nuy, Y.x, Y.y, f);
+    tell_lb<kTrack>(w, b1, nlb1, B1.x, B1.y, f);
+    tell_ub<kTrack>(w, b1, nub1, B1.x, B1.y, f);
+    tell_lb<kTrack>(w, b2, nlb2, B2.x, B2.y, f);
+    tell_ub<kTrack>(w, b2, nub2, B2.x, B2.y, f);
   }
 }
 
@@ -415,13 +462,24 @@ __device__ __forceinline__ void eval_linear_thread(const Sweep& w, int r, Flags&
   f.evals += 1;
   f.bytes += 12 + 12 * len;
   int S = 0, span = 0;
+  if (h.w & 1) {  // every coefficient positive: no sign selects
 #pragma unroll 4
-  for (int k = 0; k < len; ++k) {
-    const uint32_t t = tb.terms[base + 32 * k];
-    const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
-    const int2 D = ld_dom(st, v);
-    S += a > 0 ? a * D.x : a * D.y;
-    span = max(span, a > 0 ? a * (D.y - D.x) : a * (D.x - D.y));
+    for (int k = 0; k < len; ++k) {
+      const uint32_t t = tb.terms[base + 32 * k];
+      const int a = static_cast<int>(t) >> 16;
+      const int2 D = ld_dom(st, t & 0xffff);
+      S += a * D.x;
+      span = max(span, a * (D.y - D.x));
+    }
+  } else {
+#pragma unroll 4
+    for (int k = 0; k < len; ++k) {
+      const uint32_t t = tb.terms[base + 32 * k];
+      const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
+      const int2 D = ld_dom(st, v);
+      S += a > 0 ? a * D.x : a * D.y;
+      span = max(span, a > 0 ? a * (D.y - D.x) : a * (D.x - D.y));
+    }
   }
   if (S > c) {
     f.fl = true;
@@ -449,6 +507,7 @@ __device__ __forceinline__ void eval_linear_thread(const Sweep& w, int r, Flags&
 template <bool kTrack>
 __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags& f) {
   const Tab& tb = w.tb;
+  for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr) eval_reified_pair<kTrack>(w, tb.rfp[r], f);
   for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack>(w, tb.rf[r], f);
   for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
   for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) eval_linear_thread<kTrack>(w, r, f);
@@ -465,6 +524,18 @@ struct FixCtrl {
   int pad;
 };
 
+// Work of `it` full sweeps (every row runs in each, so the count is exact);
+// written by the team's thread 0, the only reader of the counters.
+template <bool kTrack>
+__device__ __forceinline__ void count_sweeps(const Tab& tb, const Team& tm, FixCtrl* fc, int it) {
+  if (!kTrack && tm.tid == 0) {
+    const long long ev = static_cast<long long>(it) * tb.rows_sweep;
+    const long long by = static_cast<long long>(it) * tb.bytes_sweep;
+    fc->evals = ev > 0x7fffffffll ? 0x7fffffff : static_cast<int>(ev);
+    fc->bytes = by > 0x7fffffffll ? 0x7fffffff : static_cast<int>(by);
+  }
+}
+
 // Fixed-point loop of one team on its store `st` (Sec. 5): iterate until an
 // iteration changes nothing or some tell finds an empty interval.  Failure is
 // checked inside the loop (an infeasible cycle would otherwise keep raising
@@ -480,7 +551,8 @@ struct FixCtrl {
 // buffer 0 cleared; buffer 2 cleared except for the caller's marks when
 // full = false; fc->fail, evals, bytes == 0.  The caller must not modify *fc
 // or the change buffers before the next team barrier after this returns.
-// Team-uniform return value; fc->evals / fc->bytes are valid after return.
+// Team-uniform return value; fc->evals / fc->bytes are valid after return
+// for the team's thread 0 (for every thread after the next team barrier).
 template <bool kTrack>
 __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team& tm, FixCtrl* fc,
                                              const Track& tk, bool full, int max_iter,
@@ -495,11 +567,13 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
     const Sweep w{tb, st, tk, cur, tk.chg + prv * tk.W, tk.dl + prv * tk.WL, full || !kTrack};
     Flags f{false, false, 0, 0};
     sweep_rows<kTrack>(w, tm, f);
-    const int ev = __reduce_add_sync(0xffffffffu, f.evals);
-    const int by = __reduce_add_sync(0xffffffffu, f.bytes);
-    if (tm.lane == 0) {
-      atomicAdd(&fc->evals, ev);
-      atomicAdd(&fc->bytes, by);
+    if (kTrack) {  // rows skipped vary: count what ran
+      const int ev = __reduce_add_sync(0xffffffffu, f.evals);
+      const int by = __reduce_add_sync(0xffffffffu, f.bytes);
+      if (tm.lane == 0) {
+        atomicAdd(&fc->evals, ev);
+        atomicAdd(&fc->bytes, by);
+      }
     }
     if (f.fl) st_relaxed(&fc->fail, 1);
     ++it;
@@ -507,14 +581,17 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
     const bool any = team_bar_or(tm.bar, tm.nthr, f.ch || f.fl);
     if (ld_relaxed(&fc->fail)) {
       iters = it;
+      count_sweeps<kTrack>(tb, tm, fc, it);
       return kFailed;
     }
     if (!any) break;
     if (it >= max_iter) {
       iters = it;
+      count_sweeps<kTrack>(tb, tm, fc, it);
       return kError;
     }
   }
+  count_sweeps<kTrack>(tb, tm, fc, it);
   bool empty = false;
   for (int v = tm.tid; v < tb.n_vars; v += tm.nthr) {
     const int2 D = ld_dom(st, v);

@@ -13,8 +13,8 @@ from paper_2207_12116_gb300 import _abi
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    text = open(os.path.join(ROOT, "include", "pccp.h")).read()
+def declared_functions(header="pccp.h"):
+    text = open(os.path.join(ROOT, "include", header)).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(pccp_[a-z_]+)\s*\(", text)))
 
@@ -26,6 +26,19 @@ def test_library_exports_every_declared_entry_point():
     for n in names:
         assert hasattr(lib, n), n
         assert n in _abi.SIGNATURES, f"binding lacks {n}"
+
+
+def test_probe_library_exports_every_declared_entry_point():
+    lib = _abi.load_probe()
+    names = declared_functions("pccp_probe.h")
+    assert names == ["pccp_probe"]
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _abi.PROBE_SIGNATURES, f"binding lacks {n}"
+
+
+def test_every_header_is_covered():
+    assert sorted(os.listdir(os.path.join(ROOT, "include"))) == ["pccp.h", "pccp_probe.h"]
 
 
 def test_error_strings():
