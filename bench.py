@@ -35,9 +35,13 @@ UNIT = "nodes/s"
 L2_FLUSH_BYTES = 256 << 20
 
 
+TASKS = {"tiny8": 8, "j30": 30, "j60": 60, "j120": 120}
+
+
 def workload_config(n_vars, rows, extra=None):
+    what = f"{TASKS[FAMILY]}-task" if FAMILY in TASKS else FAMILY
     cfg = {"workload": f"propagation batch: {N_NODES} search nodes (0-15 decisions each) of a "
-                       f"seeded 30-task 4-resource scheduling model ({n_vars} vars, {rows} rows)",
+                       f"seeded {what} 4-resource scheduling model ({n_vars} vars, {rows} rows)",
            "model": f"{FAMILY}/{INSTANCE}", "nodes_per_step": N_NODES, "node_seed": NODE_SEED,
            "l2": "flushed between steps (256 MB write); stores restored from pristine copies"}
     if extra:
@@ -219,11 +223,17 @@ class ClockSampler:
         return out
 
 
+def explicit_launch(args):
+    return bool(args.team or args.teams or args.ctas_per_sm or args.skip_stable
+                or args.no_stream_table)
+
+
 def launch_desc(args):
-    if not (args.team or args.teams or args.ctas_per_sm or args.skip_stable):
+    if not explicit_launch(args):
         return "library default"
     return {"team_threads": args.team, "teams_per_cta": args.teams,
-            "ctas_per_sm": args.ctas_per_sm, "skip_stable": bool(args.skip_stable)}
+            "ctas_per_sm": args.ctas_per_sm, "skip_stable": bool(args.skip_stable),
+            "stream_table": not args.no_stream_table}
 
 
 KERNEL_SOURCES = ("paper_2207_12116_gb300/csrc/k_propagate.cuh",
@@ -353,8 +363,9 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     cfg = None
-    if args.team or args.teams or args.ctas_per_sm or args.skip_stable:
-        cfg = pccp.launch_config(args.team, args.teams, args.ctas_per_sm, 0, args.skip_stable)
+    if explicit_launch(args):
+        cfg = pccp.launch_config(args.team, args.teams, args.ctas_per_sm, 0, args.skip_stable,
+                                 not args.no_stream_table)
 
     def prepare():
         lb.copy_(pristine_lb)
@@ -573,7 +584,8 @@ def run_large(args):
                      + 8 * info.n_terms) / models[0].rows
     strategy = pccp.PCCP_FIRST_FAIL
     t0 = time.perf_counter()
-    res = pccp.solve_batch(models, strategy=strategy, time_limit_ms=args.large_ms)
+    res = pccp.solve_batch(models, strategy=strategy, time_limit_ms=args.large_ms,
+                           stream_table=not args.no_stream_table)
     wall = time.perf_counter() - t0
     ms = res[0]["elapsed_ms"]
     nodes = sum(r["nodes"] for r in res)
@@ -586,7 +598,8 @@ def run_large(args):
             "row_bytes_per_s": rows * bytes_per_row / (ms / 1000),
             "kernel_ms": ms, "wall_s": wall, "nodes": nodes,
             "models_with_solution": len(found),
-            "mean_best_makespan": float(np.mean(found)) if found else None}
+            "mean_best_makespan": float(np.mean(found)) if found else None,
+            "stream_table": not args.no_stream_table}
     tbs = rows * table_per_row / (ms / 1000) / 1e9
     line["table_stream"] = {"achieved_gbs": tbs, "table_bytes": info.table_bytes}
     if not args.no_probes:
@@ -609,11 +622,17 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=8)
     ap.add_argument("--learned-nodes", type=int, default=20000)
     ap.add_argument("--learned-ms", type=int, default=20000)
+    ap.add_argument("--family", default="",
+                    help="propagation workload's model family (default j30: the headline)")
+    ap.add_argument("--nodes", type=int, default=0,
+                    help="stores per propagation step (default 10,000)")
     ap.add_argument("--no-probes", action="store_true",
                     help="skip the roofline microbenchmarks after the timed region")
     ap.add_argument("--large", action="store_true",
                     help="120-task models in one launch (own JSON line)")
     ap.add_argument("--large-models", type=int, default=1024)
+    ap.add_argument("--no-stream-table", action="store_true",
+                    help="read tables too large for shared memory in place (no TMA streaming)")
     ap.add_argument("--large-ms", type=int, default=7000)
     ap.add_argument("--search-only", action="store_true",
                     help="small search leg only (64 models x 500 nodes; parallel runs "
@@ -624,6 +643,11 @@ def main():
     ap.add_argument("--skip-stable", action="store_true",
                     help="re-run a row only after one of its variables changed")
     args = ap.parse_args()
+    global FAMILY, N_NODES
+    if args.family:  # another propagation workload (profiling and parity of other sizes)
+        FAMILY = args.family
+    if args.nodes > 0:
+        N_NODES = args.nodes
     if args.impl == "reference":
         run_reference(args)
     elif args.search_only:

@@ -114,6 +114,8 @@ typedef struct {
   int64_t bytes_per_sweep;  /* algorithmic bytes of one evaluation of every row:
                                temporal 20, reified 40, linear 12 + 12 * len */
   int32_t max_store_vars;   /* largest n_vars a single CTA can stage */
+  int32_t n_segments;       /* byte ranges of whole rows (<= 32 KB each) that one sweep
+                               streams when the table is read from global memory */
 } pccp_model_info;
 
 int pccp_model_get_info(const pccp_model* model, pccp_model_info* info);
@@ -148,6 +150,10 @@ typedef struct {
   int32_t skip_stable;    /* 1: re-run a row only after one of its variables changed
                              (change bitmaps per team; Sec. 6); 0: the eventless loop
                              of Sec. 5.  Same fixed point either way. */
+  int32_t stream_table;   /* tables too large for shared memory: 0 stream them through
+                             shared-memory buffers by TMA bulk copies, segment by
+                             segment, every sweep; -1 read rows in place (L1/L2).
+                             Same fixed point either way. */
 } pccp_launch_config;
 
 /* pccp_propagate with an explicit launch shape (cfg may be NULL) and an
@@ -192,6 +198,7 @@ typedef struct {
   int32_t blocks;        /* CTAs for the parallel search (0 = auto) */
   int32_t skip_stable;   /* as in pccp_launch_config; also lets a left child run
                             only the rows of the decided variable first */
+  int32_t stream_table;  /* as in pccp_launch_config */
   const pccp_policy* policy; /* required with PCCP_LEARNED, created on this device */
 } pccp_solve_opts;
 

@@ -45,18 +45,18 @@ class pccp_model_desc(ctypes.Structure):
 class pccp_model_info(ctypes.Structure):
     _fields_ = [("n_vars", I32), ("n_temporal", I32), ("n_linear", I32), ("n_terms", I32),
                 ("n_reified", I32), ("table_bytes", I32), ("bytes_per_sweep", I64),
-                ("max_store_vars", I32)]
+                ("max_store_vars", I32), ("n_segments", I32)]
 
 
 class pccp_launch_config(ctypes.Structure):
     _fields_ = [("team_threads", I32), ("teams_per_cta", I32), ("ctas_per_sm", I32),
-                ("max_iterations", I32), ("skip_stable", I32)]
+                ("max_iterations", I32), ("skip_stable", I32), ("stream_table", I32)]
 
 
 class pccp_solve_opts(ctypes.Structure):
     _fields_ = [("strategy", I32), ("mode", I32), ("deterministic", I32), ("obj_ub", I32),
                 ("node_limit", I64), ("time_limit_ms", I64), ("threads", I32), ("blocks", I32),
-                ("skip_stable", I32), ("policy", P)]
+                ("skip_stable", I32), ("stream_table", I32), ("policy", P)]
 
 
 class pccp_policy_weights(ctypes.Structure):

@@ -1,9 +1,11 @@
 // k_propagate.cuh -- the batched propagation kernel (included by pccp.cu).
 //
 // Persistent CTAs; the packed propagator table is brought into shared memory
-// once per CTA by TMA bulk copies; each team of warps pulls stores from a
-// global counter, stages one store (joined with the root domains) into
-// shared memory and runs the lock-free fixed-point loop on it (Sec. 4-5).
+// once per CTA by TMA bulk copies (or, when it does not fit beside a store,
+// streamed through a ring of per-team buffers every sweep); each team of warps
+// pulls stores from a global counter, stages one store (joined with the root
+// domains) into shared memory and runs the lock-free fixed-point loop on it
+// (Sec. 4-5).
 #pragma once
 
 #include "pccp_device.cuh"
@@ -26,7 +28,8 @@ struct PropArgs {
   int teams;
   int max_iter;
   int track_words;
-  int table_global;  // 1: rows are read from the device image (too big for shared memory)
+  int table_global;   // 1: rows are read from the device image (too big for shared memory)
+  int stream_stages;  // table_global: buffers of each team's stream (kStream kernels)
 };
 
 // Per-team scalars of k_propagate (shared memory).
@@ -37,13 +40,15 @@ struct PropCtrl {
 };
 
 // Instantiated for 1024-thread CTAs (one per SM) and for CTAs of up to 512
-// threads with three resident per SM (registers capped for 48 warps/SM).
-template <int kMaxThreads, int kMinBlocks, bool kTrack>
+// threads with three resident per SM (registers capped for 48 warps/SM);
+// kStream: the table is streamed (1024-thread variant only).
+template <int kMaxThreads, int kMinBlocks, bool kTrack, bool kStream>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  // shared memory: [table image, unless it is read from global memory]
+  // shared memory: [table image | kStream: one stream region per team | none]
   //                [mbarrier 16 B][PropCtrl x teams][change words x teams][stores]
-  const size_t img_bytes = a.table_global ? 0 : a.image_bytes;
+  const size_t stream_region = stream_bytes(a.stream_stages);
+  const size_t img_bytes = kStream ? stream_region * a.teams : (a.table_global ? 0 : a.image_bytes);
   uint8_t* img = smem;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + img_bytes);
   PropCtrl* ctrl_base = reinterpret_cast<PropCtrl*>(smem + img_bytes + 16);
@@ -72,6 +77,9 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   const Track tk = make_track(track_base + static_cast<size_t>(tw16) * team_id, tb.n_vars,
                               tb.n_lin + tb.n_lin_long);
   const int nv = a.n_vars;
+  Streamer stream;
+  if (kStream)  // published by the barrier at the top of the store loop
+    stream = stream_open(smem + stream_region * team_id, a.stream_stages, tb, a.image, tm, 0u);
 
   for (;;) {
     if (tm.tid == 0) ctrl->next = atomicAdd(a.counter, 1);
@@ -106,7 +114,9 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
     }
     const bool any_empty = team_bar_or(tm.bar, tm.nthr, empty);
     int status = kFailed, it = 0;
-    if (!any_empty) status = team_fixpoint<kTrack>(tb, st, tm, &ctrl->fc, tk, true, a.max_iter, it);
+    if (!any_empty)
+      status = team_fixpoint<kTrack, kStream>(tb, st, tm, &ctrl->fc, tk, true, a.max_iter, it,
+                                              &stream);
     for (int v = tm.tid; v < nv; v += tm.nthr) {
       const int2 D = st[v];
       lbs[v] = D.x;
@@ -121,6 +131,9 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
       }
     }
   }
+  // every thread passed the barrier after its last segment: the copies in
+  // flight are the prefetched ones
+  if (kStream) stream_close(stream);
 }
 
 }  // namespace pccp

@@ -55,6 +55,7 @@ struct EpsArgs {
   int obj_ub;
   int track_words;
   int table_global;  // 1: rows are read from the device image
+  int stream_stages; // table_global: buffers of each team's stream (kStream kernels)
   int x_words;       // learned strategy: feature rows per team (words)
   const PolicyDev* policy;
   int64_t node_limit;
@@ -94,11 +95,11 @@ __device__ __forceinline__ uint64_t eps_now_ns() {
 // the selection key (branch index in the low 32 bits).  Team-uniform result.
 // Broadcast slots follow the protocol of team_dfs: written before a barrier,
 // read after it, not rewritten before another barrier has passed.
-template <bool kTrack, bool kLearned>
+template <bool kTrack, bool kLearned, bool kStream>
 __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm, EpsCtrl* sc,
                                         const Track& tk, bool seeded, unsigned par,
                                         const EpsArgs& a, int& it, unsigned long long& key,
-                                        int depth, uint32_t* X) {
+                                        int depth, uint32_t* X, Streamer* stream) {
   EpsGlobal* g = a.g;
   if (tm.tid == 0) {
     int stop = ld_relaxed_gpu(&g->stop);
@@ -130,7 +131,8 @@ __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm,
   }
   team_bar(tm.bar, tm.nthr);
   if (sc->stop) return kNodeStop;
-  const int fst = team_fixpoint<kTrack>(tb, st, tm, &sc->fc, tk, !seeded, a.max_iter, it);
+  const int fst =
+      team_fixpoint<kTrack, kStream>(tb, st, tm, &sc->fc, tk, !seeded, a.max_iter, it, stream);
   if (fst == kError) return kNodeError;
   if (fst == kFailed) return kNodeFailed;
   unsigned long long* sel = &sc->sel[par];
@@ -223,13 +225,18 @@ struct EpsSmem {
   EpsCtrl* sc;
   uint32_t* track;
   int2* st;
-  uint32_t* X;  // learned strategy's feature rows
+  uint32_t* X;       // learned strategy's feature rows
+  uint8_t* stream;   // the team's stream region (streamed tables)
 };
 
+// [table image | streams: one stream region per team | none][mbarrier 16 B]
+// [EpsCtrl x teams][change words x teams][stores x teams][feature rows x teams]
 __device__ __forceinline__ EpsSmem eps_smem(uint8_t* smem, const EpsArgs& a, int team_id) {
   EpsSmem s;
-  const size_t img_bytes = a.table_global ? 0 : a.image_bytes;
+  const size_t region = stream_bytes(a.stream_stages);
+  const size_t img_bytes = a.table_global ? region * a.teams : a.image_bytes;
   s.img = smem;
+  s.stream = smem + region * team_id;
   s.mbar = reinterpret_cast<uint64_t*>(smem + img_bytes);
   EpsCtrl* ctrl = reinterpret_cast<EpsCtrl*>(smem + img_bytes + 16);
   s.sc = ctrl + team_id;
@@ -258,7 +265,7 @@ __device__ __forceinline__ Team eps_team(const EpsArgs& a, int team_id) {
 // One breadth-first level: every input path is propagated once; failures
 // and solutions are counted; every other node pushes its two children
 // (left ub <= m, right lb >= m + 1) to the output level.
-template <bool kTrack, bool kLearned>
+template <bool kTrack, bool kLearned, bool kStream>
 __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
@@ -276,6 +283,9 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
   const Tab tb = make_tab(a.table_global ? a.image : sm.img);
   const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
+  Streamer stream;
+  if (kStream)  // published by the barrier at the top of the work loop
+    stream = stream_open(sm.stream, a.stream_stages, tb, a.image, tm, 0u);
   EpsCtrl* sc = sm.sc;
   unsigned long long nodes = 0, published = 0, fails = 0, sols = 0, iters = 0, evals = 0;
   int max_d = 0;
@@ -289,7 +299,8 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
     eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, tk, path, a.in_len);
     int it = 0;
     unsigned long long key = 0;
-    const int r = eps_node<kTrack, kLearned>(tb, sm.st, tm, sc, tk, false, par, a, it, key, a.in_len, sm.X);
+    const int r = eps_node<kTrack, kLearned, kStream>(tb, sm.st, tm, sc, tk, false, par, a, it, key,
+                                                        a.in_len, sm.X, &stream);
     par ^= 1u;
     if (r == kNodeStop) break;
     if (tm.tid == 0) {
@@ -337,6 +348,8 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
       a.out_paths[static_cast<size_t>(o + 1) * w + k] = e;
     }
   }
+  // every exit follows a team barrier after the team's last segment
+  if (kStream) stream_close(stream);
   if (tm.tid == 0) {
     atomicAdd(&a.g->nodes, nodes);
     atomicAdd(&a.g->fails, fails);
@@ -348,7 +361,7 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
 }
 
 // Persistent teams search the subtrees under the frontier paths depth first.
-template <bool kTrack, bool kLearned>
+template <bool kTrack, bool kLearned, bool kStream>
 __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
@@ -366,6 +379,9 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
   const Tab tb = make_tab(a.table_global ? a.image : sm.img);
   const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
+  Streamer stream;
+  if (kStream)  // published by the barrier at the top of the work loop
+    stream = stream_open(sm.stream, a.stream_stages, tb, a.image, tm, 0u);
   EpsCtrl* sc = sm.sc;
   int2* stack = a.stacks + static_cast<size_t>(team_gid) * a.max_depth;
   const int base = a.in_len;
@@ -386,7 +402,8 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
     for (;;) {
       int it = 0;
       unsigned long long key = 0;
-      const int r = eps_node<kTrack, kLearned>(tb, sm.st, tm, sc, tk, seeded, par, a, it, key, depth, sm.X);
+      const int r = eps_node<kTrack, kLearned, kStream>(tb, sm.st, tm, sc, tk, seeded, par, a, it,
+                                                          key, depth, sm.X, &stream);
       par ^= 1u;
       if (r == kNodeStop) {
         done = true;
@@ -452,6 +469,8 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
       seeded = false;
     }
   }
+  // every exit follows a team barrier after the team's last segment
+  if (kStream) stream_close(stream);
   if (tm.tid == 0) {
     atomicAdd(&a.g->nodes, nodes);
     atomicAdd(&a.g->fails, fails);

@@ -83,6 +83,7 @@ struct SolveArgs {
   uint32_t max_image_bytes;  // 0 when the tables are read from global memory
   int max_track_words;
   int table_global;
+  int stream_stages;          // table_global: buffers of the stream (kStream kernels)
   int x_words;                // learned strategy: feature rows per team (words)
   int max_vars_smem;          // store slots reserved per CTA
   const PolicyDev* policy;
@@ -112,10 +113,11 @@ constexpr uint32_t kRightBit = 0x80000000u;
 // All control decisions are made by thread 0 and broadcast through shared
 // memory; every broadcast slot is written before a barrier and read after it,
 // and never rewritten before the next barrier that follows all its reads.
-template <bool kTrack, bool kLearned>
+template <bool kTrack, bool kLearned, bool kStream>
 __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st, const Team& tm,
                          SearchCtrl* sc, const Track& tk, int2* stack, const SolveArgs& a,
-                         int max_iter, int32_t* witness, InstanceResult* out, uint32_t* X) {
+                         int max_iter, int32_t* witness, InstanceResult* out, uint32_t* X,
+                         Streamer* stream) {
   const int nv = tb.n_vars;
   const uint64_t t0 = globaltimer_ns();
   // thread-0 state
@@ -156,7 +158,8 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
     team_bar(tm.bar, tm.nthr);  // N1
     if (sc->stop) break;
     int it = 0;
-    const int fst = team_fixpoint<kTrack>(tb, st, tm, &sc->fc, tk, !seeded, max_iter, it);
+    const int fst =
+        team_fixpoint<kTrack, kStream>(tb, st, tm, &sc->fc, tk, !seeded, max_iter, it, stream);
     if (tm.tid == 0) {
       ++nodes;
       iters += it;
@@ -278,14 +281,17 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
   }
 }
 
-template <bool kTrack, bool kLearned>
+template <bool kTrack, bool kLearned, bool kStream>
 __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
+  // [table image | kStream: the stream region | none][mbarrier][SearchCtrl]
+  // [change words][store][feature rows]
+  const size_t head = kStream ? stream_bytes(a.stream_stages) : a.max_image_bytes;
   uint8_t* img = smem;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + a.max_image_bytes);
-  SearchCtrl* sc = reinterpret_cast<SearchCtrl*>(smem + a.max_image_bytes + 16);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + head);
+  SearchCtrl* sc = reinterpret_cast<SearchCtrl*>(smem + head + 16);
   uint32_t* track_base =
-      reinterpret_cast<uint32_t*>(smem + a.max_image_bytes + 16 + sizeof(SearchCtrl));
+      reinterpret_cast<uint32_t*>(smem + head + 16 + sizeof(SearchCtrl));
   int2* st = reinterpret_cast<int2*>(track_base + ((a.max_track_words + 3) & ~3));
   uint32_t* X = reinterpret_cast<uint32_t*>(st + a.max_vars_smem);
   if (threadIdx.x == 0) mbar_init(mbar, 1);
@@ -298,6 +304,9 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
   tm.nwarps = blockDim.x >> 5;
   int2* stack = a.stacks + static_cast<size_t>(blockIdx.x) * a.max_depth;
   uint32_t parity = 0;
+  Streamer stream;
+  bool open = false;
+  uint32_t seq = 0;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) sc->next = atomicAdd(a.counter, 1);
@@ -319,9 +328,16 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
     }
     const Tab tb = make_tab(a.table_global ? d.image : img);
     const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
-    team_dfs<kTrack, kLearned>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
-                               a.witness + d.witness_off, &a.res[i], X);
+    if (kStream) {  // the previous model's prefetched copies land first
+      if (open) seq = stream_close(stream);
+      stream = stream_open(img, a.stream_stages, tb, d.image, tm, seq);
+      open = true;
+      __syncthreads();
+    }
+    team_dfs<kTrack, kLearned, kStream>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
+                                        a.witness + d.witness_off, &a.res[i], X, &stream);
   }
+  if (kStream && open) stream_close(stream);
 }
 
 // -------------------------------------------------------------- host model
@@ -329,6 +345,7 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
 struct Packed {
   std::vector<uint8_t> image;  // header + sections, 16-byte aligned sizes
   int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective;
+  int32_t n_seg;
   int64_t bytes_per_sweep;
 };
 
@@ -345,6 +362,7 @@ const PolicyDev* policy_dev(const pccp_policy* p);
 struct pccp_model {
   int device;
   int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective;
+  int32_t n_seg;  // stream segments of the table
   uint32_t image_bytes;
   int64_t bytes_per_sweep;
   int32_t max_iter;  // every changing iteration narrows some bound by >= 1
@@ -469,11 +487,13 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   });
   std::vector<int4> L, LL;
   std::vector<uint32_t> TERMS, TERMS_LONG;
+  std::vector<size_t> tile_start;  // first term of each tile, then the end
   for (size_t t0 = 0; t0 < short_rows.size(); t0 += 32) {
     const size_t t1 = std::min(short_rows.size(), t0 + 32);
     size_t maxlen = 0;
     for (size_t r = t0; r < t1; ++r) maxlen = std::max(maxlen, short_rows[r].terms.size());
     const size_t tile = TERMS.size();
+    tile_start.push_back(tile);
     TERMS.resize(tile + 32 * maxlen, 0u);
     for (size_t r = t0; r < t1; ++r) {
       const LinRow& row = short_rows[r];
@@ -485,6 +505,7 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
                             static_cast<int32_t>(row.terms.size()), pos ? 1 : 0));
     }
   }
+  tile_start.push_back(TERMS.size());
   for (const LinRow& row : long_rows) {
     LL.push_back(make_int4(row.c, static_cast<int32_t>(TERMS_LONG.size()),
                            static_cast<int32_t>(row.terms.size()), 0));
@@ -572,6 +593,57 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   off = align16(off + ADJ.size() * sizeof(int32_t));
   h.off_bstat = static_cast<int32_t>(off);
   off = align16(off + BST.size() * sizeof(BranchStatic));
+  // Stream segments: the row sections cut into byte ranges of whole rows of
+  // at most kStreamChunk bytes, 16-byte aligned (a range may run into the
+  // section's padding), in the order a sweep evaluates them.
+  std::vector<StreamSeg> SEG;
+  auto seg = [&SEG](int32_t kind, size_t first, size_t count, size_t src, size_t bytes,
+                    size_t term_base) {
+    StreamSeg s;
+    std::memset(&s, 0, sizeof(s));
+    s.kind = kind;
+    s.first = static_cast<int32_t>(first);
+    s.count = static_cast<int32_t>(count);
+    s.src_off = static_cast<int32_t>(src);
+    s.bytes = static_cast<int32_t>(bytes);
+    s.term_base = static_cast<int32_t>(term_base);
+    SEG.push_back(s);
+  };
+  auto fixed_rows = [&seg](int32_t kind, size_t n, size_t rec, size_t section) {
+    const size_t per = kStreamChunk / rec;
+    for (size_t f = 0; f < n; f += per) {
+      const size_t c = std::min(per, n - f);
+      seg(kind, f, c, section + f * rec, align16(c * rec), 0);
+    }
+  };
+  fixed_rows(kSegPairs, RFP.size(), sizeof(uint4), static_cast<size_t>(h.off_rfp));
+  fixed_rows(kSegSingles, RF.size(), sizeof(uint2), static_cast<size_t>(h.off_rf));
+  fixed_rows(kSegTemporal, T.size(), sizeof(uint2), static_cast<size_t>(h.off_t));
+  const size_t n_tiles = tile_start.size() - 1;
+  for (size_t t0 = 0; t0 < n_tiles;) {  // whole tiles (a tile is at most 8 KB)
+    size_t t1 = t0 + 1;
+    while (t1 < n_tiles && 4 * (tile_start[t1 + 1] - tile_start[t0]) <= kStreamChunk) ++t1;
+    const size_t rows = std::min(L.size(), 32 * t1) - 32 * t0;
+    seg(kSegShort, 32 * t0, rows, h.off_terms + 4 * tile_start[t0],
+        4 * (tile_start[t1] - tile_start[t0]), tile_start[t0]);
+    t0 = t1;
+  }
+  for (size_t r0 = 0; r0 < LL.size();) {  // whole long rows
+    const size_t start = (4 * static_cast<size_t>(LL[r0].y)) & ~static_cast<size_t>(15);
+    auto end_of = [&LL](size_t r) { return align16(4 * static_cast<size_t>(LL[r].y + LL[r].z)); };
+    if (end_of(r0) - start > static_cast<size_t>(kStreamChunk)) {
+      seg(kSegLongGlobal, r0, 1, 0, 0, 0);  // longer than a chunk: read in place
+      ++r0;
+      continue;
+    }
+    size_t r1 = r0 + 1;
+    while (r1 < LL.size() && end_of(r1) - start <= static_cast<size_t>(kStreamChunk)) ++r1;
+    seg(kSegLong, r0, r1 - r0, h.off_terms_long + start, end_of(r1 - 1) - start, start / 4);
+    r0 = r1;
+  }
+  h.off_seg = static_cast<int32_t>(off);
+  h.n_seg = static_cast<int32_t>(SEG.size());
+  off = align16(off + SEG.size() * sizeof(StreamSeg));
   if (off > (1u << 30)) return PCCP_ERR_UNSUPPORTED;
   h.image_bytes = static_cast<int32_t>(off);
 
@@ -596,6 +668,8 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
     std::memcpy(p->image.data() + h.off_adj, ADJ.data(), ADJ.size() * sizeof(int32_t));
   if (!BST.empty())
     std::memcpy(p->image.data() + h.off_bstat, BST.data(), BST.size() * sizeof(BranchStatic));
+  if (!SEG.empty())
+    std::memcpy(p->image.data() + h.off_seg, SEG.data(), SEG.size() * sizeof(StreamSeg));
   p->n_vars = h.n_vars;
   p->n_t = h.n_t;
   p->n_rf = h.n_rf + 2 * h.n_rfp;
@@ -604,6 +678,7 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   p->n_branch = h.n_branch;
   p->objective = h.objective;
   p->bytes_per_sweep = bytes_per_sweep;
+  p->n_seg = h.n_seg;
   return PCCP_OK;
 }
 
@@ -615,13 +690,31 @@ size_t solve_smem(uint32_t max_img, int max_track_words, int max_vars, int x_wor
          static_cast<size_t>(max_vars) * sizeof(int2) + 4 * static_cast<size_t>(x_words);
 }
 
+// Stream buffers per team for a table read from global memory: the most
+// (3, else 2) that fit beside `teams` teams of `per_team` bytes; 0 when the
+// table has no rows, streaming is switched off, or not even two fit.
+int stream_stages_for(int n_seg, int stream_opt, size_t fixed, size_t per_team, int teams,
+                      int smem_max) {
+  if (n_seg <= 0 || stream_opt < 0) return 0;
+  for (int s = kStreamMaxStages; s >= 2; --s)
+    if (fixed + static_cast<size_t>(teams) * (per_team + stream_bytes(s)) <=
+        static_cast<size_t>(smem_max))
+      return s;
+  return 0;
+}
+
 // Shared memory of k_solve, with the tables in shared memory when they fit,
-// else read from the device images (*global = true).
+// else read from the device images (*global = true), streamed through
+// *stages buffers when the largest segment list is non-empty and they fit.
 size_t plan_solve_smem(uint32_t max_img, int max_track_words, int max_vars, int smem_max,
-                       bool* global, int x_words = 0) {
+                       bool* global, int x_words, int stream_opt, int max_seg, int* stages) {
   const size_t with = solve_smem(max_img, max_track_words, max_vars, x_words);
   *global = with > static_cast<size_t>(smem_max);
-  return *global ? solve_smem(0, max_track_words, max_vars, x_words) : with;
+  *stages = 0;
+  if (!*global) return with;
+  const size_t base = solve_smem(0, max_track_words, max_vars, x_words);
+  *stages = stream_stages_for(max_seg, stream_opt, base, 0, 1, smem_max);
+  return base + stream_bytes(*stages);
 }
 
 // Words of shared memory for the learned strategy's feature rows (0 otherwise).
@@ -629,11 +722,16 @@ int policy_x_words(const pccp_solve_opts* o, int max_branch) {
   return o->strategy == PCCP_LEARNED ? 8 * ((max_branch + 15) & ~15) : 0;
 }
 
-// The k_solve instantiation for a search's options.
+// The k_solve instantiation for a search's options (stream: the tables are
+// streamed).
 using SolveKernel = void (*)(SolveArgs);
-SolveKernel solve_kernel(const pccp_solve_opts* o) {
-  if (o->strategy == PCCP_LEARNED) return k_solve<false, true>;
-  return o->skip_stable ? k_solve<true, false> : k_solve<false, false>;
+SolveKernel solve_kernel(const pccp_solve_opts* o, bool stream) {
+  if (stream) {
+    if (o->strategy == PCCP_LEARNED) return k_solve<false, true, true>;
+    return o->skip_stable ? k_solve<true, false, true> : k_solve<false, false, true>;
+  }
+  if (o->strategy == PCCP_LEARNED) return k_solve<false, true, false>;
+  return o->skip_stable ? k_solve<true, false, false> : k_solve<false, false, false>;
 }
 
 // Strategy and policy checks shared by the search entry points.
@@ -683,6 +781,7 @@ int check_device(const pccp_model* m) {
 struct PropPlan {
   void (*kern)(PropArgs);
   bool table_global;
+  int stages;  // stream buffers per team (0: rows read in place)
   int team, teams, grid;
   size_t smem;
 };
@@ -712,11 +811,16 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   teams = std::min({teams, fit, 1024 / team});
   if (cfg && cfg->teams_per_cta > 0 && teams < cfg->teams_per_cta) return PCCP_ERR_SMEM;
   if (teams < 1) return PCCP_ERR_SMEM;
-  const size_t smem = base + static_cast<size_t>(teams) * per_team;
+  const int stages = global ? stream_stages_for(m->n_seg, cfg ? cfg->stream_table : 0, base,
+                                                per_team, teams, smem_max)
+                            : 0;
+  const size_t smem = base + static_cast<size_t>(teams) * (per_team + stream_bytes(stages));
   const bool track = cfg && cfg->skip_stable;
-  const auto kern = (teams * team <= 512)
-                        ? (track ? k_propagate<512, 3, true> : k_propagate<512, 3, false>)
-                        : (track ? k_propagate<1024, 1, true> : k_propagate<1024, 1, false>);
+  const auto kern =
+      stages > 0 ? (track ? k_propagate<1024, 1, true, true> : k_propagate<1024, 1, false, true>)
+      : (teams * team <= 512)
+          ? (track ? k_propagate<512, 3, true, false> : k_propagate<512, 3, false, false>)
+          : (track ? k_propagate<1024, 1, true, false> : k_propagate<1024, 1, false, false>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -733,6 +837,7 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   const int want = (n_stores + teams - 1) / teams;
   p->kern = kern;
   p->table_global = global;
+  p->stages = stages;
   p->team = team;
   p->teams = teams;
   p->grid = std::max(1, std::min(want, sms * per_sm));
@@ -778,6 +883,7 @@ int pccp_model_create(const pccp_model_desc* desc, pccp_model** out) {
   m->objective = p.objective;
   m->image_bytes = static_cast<uint32_t>(p.image.size());
   m->bytes_per_sweep = p.bytes_per_sweep;
+  m->n_seg = p.n_seg;
   {
     // total width of the root box + 3 bounds the iterations of any store
     int64_t w = 3;
@@ -829,6 +935,7 @@ int pccp_model_get_info(const pccp_model* m, pccp_model_info* info) {
   const int smem_max = max_dyn_smem();
   int64_t room = static_cast<int64_t>(smem_max) - m->image_bytes - 32;
   info->max_store_vars = room > 0 ? static_cast<int32_t>(std::min<int64_t>(room / 8, 65535)) : 0;
+  info->n_segments = m->n_seg;
   return PCCP_OK;
 }
 
@@ -864,6 +971,7 @@ int pccp_propagate_ex(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_
   a.track_words = track_words(m->n_vars, m->n_lin);
   a.work = work;
   a.table_global = plan.table_global ? 1 : 0;
+  a.stream_stages = plan.stages;
   plan.kern<<<plan.grid, plan.team * plan.teams, plan.smem, s>>>(a);
   const cudaError_t le = cudaGetLastError();
   cudaFreeAsync(counter, s);
@@ -892,7 +1000,7 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
 
   std::vector<InstanceDesc> desc(n_models);
   uint32_t max_img = 0;
-  int32_t max_vars = 0, max_branch = 0, max_tw = 0;
+  int32_t max_vars = 0, max_branch = 0, max_tw = 0, max_seg = 0;
   int64_t wit_total = 0;
   for (int32_t i = 0; i < n_models; ++i) {
     const pccp_model* m = models[i];
@@ -912,13 +1020,16 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     max_vars = std::max(max_vars, m->n_vars);
     max_branch = std::max(max_branch, m->n_branch);
     max_tw = std::max(max_tw, track_words(m->n_vars, m->n_lin));
+    max_seg = std::max(max_seg, m->n_seg);
   }
   bool global = false;
+  int stages = 0;
   const int xw = policy_x_words(opts, max_branch);
-  const size_t smem = plan_solve_smem(max_img, max_tw, max_vars, smem_max, &global, xw);
+  const size_t smem = plan_solve_smem(max_img, max_tw, max_vars, smem_max, &global, xw,
+                                      opts->stream_table, max_seg, &stages);
   if (smem > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   if (global && opts->threads <= 0) threads = 1024;
-  const auto ksolve = solve_kernel(opts);
+  const auto ksolve = solve_kernel(opts, stages > 0);
   PCCP_CUDA(cudaFuncSetAttribute(ksolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
   int per_sm = 0;
@@ -969,6 +1080,7 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     a.max_image_bytes = global ? 0 : max_img;
     a.max_track_words = max_tw;
     a.table_global = global ? 1 : 0;
+    a.stream_stages = stages;
     a.x_words = xw;
     a.max_vars_smem = max_vars;
     a.policy = opts->strategy == PCCP_LEARNED ? policy_dev(opts->policy) : nullptr;
@@ -1048,12 +1160,25 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   if (global && o->threads <= 0) team = 1024;
   const int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
   const int teams = std::max(1, std::min({8, fit, 1024 / team}));
-  const size_t smem = base + static_cast<size_t>(teams) * per_team;
+  const int stages =
+      global ? stream_stages_for(m->n_seg, o->stream_table, base, per_team, teams, smem_max) : 0;
+  const size_t smem = base + static_cast<size_t>(teams) * (per_team + stream_bytes(stages));
   const bool learned = o->strategy == PCCP_LEARNED;
-  const auto kexp = learned ? k_eps_expand<false, true>
-                            : (o->skip_stable ? k_eps_expand<true, false> : k_eps_expand<false, false>);
-  const auto ksol = learned ? k_eps_solve<false, true>
-                            : (o->skip_stable ? k_eps_solve<true, false> : k_eps_solve<false, false>);
+  using EpsKernel = void (*)(EpsArgs);
+  EpsKernel kexp, ksol;
+  if (stages > 0) {
+    kexp = learned ? k_eps_expand<false, true, true>
+                   : (o->skip_stable ? k_eps_expand<true, false, true> : k_eps_expand<false, false, true>);
+    ksol = learned ? k_eps_solve<false, true, true>
+                   : (o->skip_stable ? k_eps_solve<true, false, true> : k_eps_solve<false, false, true>);
+  } else {
+    kexp = learned ? k_eps_expand<false, true, false>
+                   : (o->skip_stable ? k_eps_expand<true, false, false>
+                                     : k_eps_expand<false, false, false>);
+    ksol = learned ? k_eps_solve<false, true, false>
+                   : (o->skip_stable ? k_eps_solve<true, false, false>
+                                     : k_eps_solve<false, false, false>);
+  }
   PCCP_CUDA(cudaFuncSetAttribute(kexp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
   PCCP_CUDA(cudaFuncSetAttribute(ksol, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1120,6 +1245,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     a.obj_ub = o->obj_ub;
     a.track_words = track_words(m->n_vars, m->n_lin);
     a.table_global = global ? 1 : 0;
+    a.stream_stages = stages;
     a.x_words = xw;
     a.policy = o->strategy == PCCP_LEARNED ? policy_dev(o->policy) : nullptr;
     a.node_limit = o->node_limit;

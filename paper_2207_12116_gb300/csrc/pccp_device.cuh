@@ -19,7 +19,7 @@ namespace pccp {
 
 enum : int { kFixpoint = 0, kFailed = 1, kError = 2 };
 
-// Header at the start of the packed table image (64 bytes).  The image is
+// Header at the start of the packed table image (112 bytes).  The image is
 // copied verbatim into shared memory, so every offset is relative to its start
 // and 16-byte aligned.
 struct TableHeader {
@@ -28,8 +28,32 @@ struct TableHeader {
   int32_t off_adj_off, off_adj, n_adj, off_bstat, off_rfp, n_rfp;
   int32_t rows_sweep;   // row evaluations in one full sweep (a reified pair counts 2)
   int32_t bytes_sweep;  // their algorithmic bytes
+  int32_t off_seg, n_seg;  // stream segments (tables read from global memory)
+  int32_t pad[2];
 };
-static_assert(sizeof(TableHeader) == 96, "header must be 96 bytes");
+static_assert(sizeof(TableHeader) == 112, "header must be 112 bytes");
+
+// Streamed tables.  When a table does not fit in shared memory beside a store,
+// a sweep brings its rows in as a cyclic sequence of segments of at most
+// kStreamChunk bytes, each a byte range of the image holding whole rows of one
+// kind, copied by TMA bulk copies into a ring of per-team buffers.
+constexpr int kStreamChunk = 32768;
+constexpr int kStreamMaxStages = 3;
+enum : int32_t {
+  kSegPairs = 0,      // reified pairs (uint4)
+  kSegSingles = 1,    // single reified rows (uint2)
+  kSegTemporal = 2,   // temporal rows (uint2)
+  kSegShort = 3,      // whole tiles of short linear rows: their terms
+  kSegLong = 4,       // whole long linear rows: their terms
+  kSegLongGlobal = 5  // long rows longer than a chunk: terms read from global memory
+};
+struct StreamSeg {
+  int32_t kind, first, count;  // rows first .. first + count - 1 of that kind
+  int32_t src_off, bytes;      // byte range of the image (16-byte aligned; bytes may be 0)
+  int32_t term_base;           // kSegShort / kSegLong: term index at src_off
+  int32_t pad[2];
+};
+static_assert(sizeof(StreamSeg) == 32, "segment record must be 32 bytes");
 
 // Row encodings (structure of arrays, one array per row kind):
 //   temporal  uint2 {x | y << 16, d}              x + d <= y
@@ -57,6 +81,8 @@ struct Tab {
   const float* bstat;       // [n_branch][8] static features of the branch variables
   int n_vars, n_t, n_rf, n_rfp, n_lin, n_lin_long, n_terms, n_branch, objective;
   int rows_sweep, bytes_sweep;
+  const StreamSeg* seg;
+  int n_seg;
 };
 
 __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
@@ -83,6 +109,8 @@ __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
   tb.n_rfp = h->n_rfp;
   tb.rows_sweep = h->rows_sweep;
   tb.bytes_sweep = h->bytes_sweep;
+  tb.seg = reinterpret_cast<const StreamSeg*>(img + h->off_seg);
+  tb.n_seg = h->n_seg;
   tb.rfp = reinterpret_cast<const uint4*>(img + h->off_rfp);
   return tb;
 }
@@ -148,6 +176,63 @@ __device__ __forceinline__ bool team_bar_or(int id, int n, bool p) {
 
 __device__ __forceinline__ void team_bar(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// ------------------------------------------------------------ mbarrier / TMA bulk copy
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count)
+               : "memory");
+}
+
+// Plain arrive (count 1) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Make mbarrier initialisation visible to the async proxy (TMA completions).
+__device__ __forceinline__ void fence_mbarrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1-D TMA bulk copy global -> shared, completing `bytes` on the mbarrier.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: true when the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity, int max_tries) {
+  for (int i = 0; i < max_tries; ++i)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
 }
 
 // ------------------------------------------------------------ team context
@@ -385,24 +470,30 @@ __device__ __forceinline__ void eval_reified_pair(const Sweep& w, uint4 row, Fla
 // registers; longer rows reload theirs (a fresher bound only weakens the
 // tell, which stays sound, and the last iteration sees a stable store).
 template <bool kTrack>
-__device__ __forceinline__ void eval_linear_warp(const Sweep& w, int r, int lane, Flags& f) {
-  const Tab& tb = w.tb;
-  int2* st = w.st;
-  if (kTrack && !w.full && !test_bit(w.prev_dl, tb.n_lin + r)) {
+__device__ __forceinline__ bool skip_linear_long(const Sweep& w, int r, int lane, Flags& f) {
+  if (kTrack && !w.full && !test_bit(w.prev_dl, w.tb.n_lin + r)) {
     if (lane == 0) f.bytes += 4;
-    return;
+    return true;
   }
-  const int4 h = tb.lin_long[r];
+  return false;
+}
+
+// Long row r with header h; its term k at tp[k] (shared or global memory).
+template <bool kTrack>
+__device__ __forceinline__ void eval_linear_warp_at(const Sweep& w, int4 h,
+                                                    const uint32_t* __restrict__ tp, int lane,
+                                                    Flags& f) {
+  int2* st = w.st;
   if (lane == 0) {
     f.evals += 1;
     f.bytes += 12 + 12 * h.z;
   }
-  const int c = h.x, off = h.y, len = h.z;
+  const int c = h.x, len = h.z;
   int S = 0, span = 0;
   int v0 = 0, a0 = 0;
   int2 D0 = make_int2(0, 0);
   for (int k = lane; k < len; k += 32) {
-    const uint32_t t = tb.terms_long[off + k];
+    const uint32_t t = tp[k];
     const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
     const int2 D = ld_dom(st, v);
     const int mt = a > 0 ? a * D.x : a * D.y;
@@ -430,7 +521,7 @@ __device__ __forceinline__ void eval_linear_warp(const Sweep& w, int r, int lane
       a = a0;
       D = D0;
     } else {
-      const uint32_t t = tb.terms_long[off + k];
+      const uint32_t t = tp[k];
       v = t & 0xffff;
       a = static_cast<int>(t) >> 16;
       D = ld_dom(st, v);
@@ -450,22 +541,27 @@ __device__ __forceinline__ void eval_linear_warp(const Sweep& w, int r, int lane
 // passes as eval_linear_warp with the sum kept in a register (no warp
 // reduction and no idle lanes on rows shorter than a warp).
 template <bool kTrack>
-__device__ __forceinline__ void eval_linear_thread(const Sweep& w, int r, Flags& f) {
-  const Tab& tb = w.tb;
-  int2* st = w.st;
+__device__ __forceinline__ bool skip_linear_short(const Sweep& w, int r, Flags& f) {
   if (kTrack && !w.full && !test_bit(w.prev_dl, r)) {
     f.bytes += 4;
-    return;
+    return true;
   }
-  const int4 h = tb.lin[r];
-  const int c = h.x, base = h.y, len = h.z;
+  return false;
+}
+
+// Short row with header h; its term k at tp[32 k] (shared or global memory).
+template <bool kTrack>
+__device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
+                                                      const uint32_t* __restrict__ tp, Flags& f) {
+  int2* st = w.st;
+  const int c = h.x, len = h.z;
   f.evals += 1;
   f.bytes += 12 + 12 * len;
   int S = 0, span = 0;
   if (h.w & 1) {  // every coefficient positive: no sign selects
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
-      const uint32_t t = tb.terms[base + 32 * k];
+      const uint32_t t = tp[32 * k];
       const int a = static_cast<int>(t) >> 16;
       const int2 D = ld_dom(st, t & 0xffff);
       S += a * D.x;
@@ -474,7 +570,7 @@ __device__ __forceinline__ void eval_linear_thread(const Sweep& w, int r, Flags&
   } else {
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
-      const uint32_t t = tb.terms[base + 32 * k];
+      const uint32_t t = tp[32 * k];
       const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
       const int2 D = ld_dom(st, v);
       S += a > 0 ? a * D.x : a * D.y;
@@ -487,7 +583,7 @@ __device__ __forceinline__ void eval_linear_thread(const Sweep& w, int r, Flags&
   }
   if (S + span <= c) return;
   for (int k = 0; k < len; ++k) {
-    const uint32_t t = tb.terms[base + 32 * k];
+    const uint32_t t = tp[32 * k];
     const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
     const int2 D = ld_dom(st, v);
     const int mt = a > 0 ? a * D.x : a * D.y;
@@ -510,9 +606,201 @@ __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags
   for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr) eval_reified_pair<kTrack>(w, tb.rfp[r], f);
   for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack>(w, tb.rf[r], f);
   for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
-  for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) eval_linear_thread<kTrack>(w, r, f);
-  for (int r = tm.warp; r < tb.n_lin_long; r += tm.nwarps)
-    eval_linear_warp<kTrack>(w, r, tm.lane, f);
+  for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) {
+    if (skip_linear_short<kTrack>(w, r, f)) continue;
+    const int4 h = tb.lin[r];
+    eval_linear_thread_at<kTrack>(w, h, tb.terms + h.y, f);
+  }
+  for (int r = tm.warp; r < tb.n_lin_long; r += tm.nwarps) {
+    if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
+    const int4 h = tb.lin_long[r];
+    eval_linear_warp_at<kTrack>(w, h, tb.terms_long + h.y, tm.lane, f);
+  }
+}
+
+// ------------------------------------------------------------ streamed sweep
+
+// Per-team control words of a stream (shared memory, 64 bytes), followed by
+// the team's ring of `stages` buffers of kStreamChunk bytes.
+struct StreamCtl {
+  uint64_t full[kStreamMaxStages];  // phase k of full[b]: the k-th copy into buffer b landed
+  uint32_t done[kStreamMaxStages];  // warps finished with the segment in buffer b
+  int32_t err;                      // a wait gave up (set by any thread)
+  int32_t pad;
+};
+static_assert(sizeof(StreamCtl) == 48, "stream control words");
+constexpr int kStreamCtlBytes = 128;  // keeps the buffers 128-byte aligned
+
+__host__ __device__ __forceinline__ size_t stream_bytes(int stages) {
+  return stages > 0 ? kStreamCtlBytes + static_cast<size_t>(stages) * kStreamChunk : 0;
+}
+
+// A team's view of its stream.  g numbers the segments consumed by the team
+// since the kernel started (team-uniform: every thread steps it identically);
+// segment q is seg[(q - q0) % n_seg] of the image opened at q0, it lands in
+// buffer q % stages, and its copy is phase q / stages of that buffer's
+// mbarrier.  A sweep consumes exactly n_seg segments, so it starts at
+// segment 0.  Invariant between segments: the copies of the next `stages`
+// segments have been issued, or will be by the last warp to finish the
+// segment before them.
+struct Streamer {
+  StreamCtl* ctl;
+  uint8_t* buf;
+  const uint8_t* image;  // device image (global memory)
+  const StreamSeg* seg;  // its segment list (global memory)
+  int n_seg;
+  int stages;
+  uint32_t g;
+  uint32_t q0;
+};
+
+// Wait limit of a stream copy: far above any copy's latency.
+constexpr unsigned long long kStreamWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for an mbarrier phase, giving up after kStreamWaitNs of wall time.
+__device__ __forceinline__ bool mbar_wait_timed(uint64_t* mbar, uint32_t parity) {
+  if (mbar_try_wait(mbar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(mbar, parity)) return true;
+    if (now_ns() - t0 > kStreamWaitNs) return false;
+  }
+}
+
+// Issue the copy of sequence number q (one thread).
+__device__ __forceinline__ void stream_issue(const Streamer& sm, uint32_t q) {
+  const StreamSeg s = sm.seg[(q - sm.q0) % static_cast<uint32_t>(sm.n_seg)];
+  const int b = static_cast<int>(q % static_cast<uint32_t>(sm.stages));
+  uint64_t* mb = &sm.ctl->full[b];
+  if (s.bytes > 0) {
+    fence_proxy_async_smem();  // earlier generic reads of the buffer come first
+    mbar_arrive_expect_tx(mb, static_cast<uint32_t>(s.bytes));
+    bulk_copy_g2s(sm.buf + static_cast<size_t>(b) * kStreamChunk, sm.image + s.src_off,
+                  static_cast<uint32_t>(s.bytes), mb);
+  } else {
+    mbar_arrive(mb);  // nothing to copy: complete the phase
+  }
+}
+
+// Open a stream on an image: thread 0 of the team initialises the control
+// words and issues the first `stages` copies.  The caller passes a team
+// barrier before any thread consumes a segment.  A stream is closed with
+// stream_close before it is reopened or the CTA exits.
+__device__ __forceinline__ Streamer stream_open(uint8_t* region, int stages, const Tab& tb,
+                                                const uint8_t* image, const Team& tm,
+                                                uint32_t g0) {
+  Streamer sm;
+  sm.ctl = reinterpret_cast<StreamCtl*>(region);
+  sm.buf = region + kStreamCtlBytes;
+  sm.image = image;
+  sm.seg = tb.seg;
+  sm.n_seg = tb.n_seg;
+  sm.stages = tb.n_seg > 0 ? stages : 0;
+  sm.g = g0;
+  sm.q0 = g0;
+  if (tm.tid == 0 && sm.stages > 0) {
+    if (g0 == 0) {
+      for (int b = 0; b < kStreamMaxStages; ++b) {
+        mbar_init(&sm.ctl->full[b], 1);
+        sm.ctl->done[b] = 0u;
+      }
+      sm.ctl->err = 0;
+      fence_mbarrier_init();
+    }
+    for (int i = 0; i < sm.stages; ++i) stream_issue(sm, sm.g + static_cast<uint32_t>(i));
+  }
+  return sm;
+}
+
+// Wait for the copies still in flight (the next `stages` segments).  Called
+// by every thread of the team after a team barrier that follows the last
+// segment consumed.  Returns the sequence number to reopen from.
+__device__ __forceinline__ uint32_t stream_close(const Streamer& sm) {
+  for (int i = 0; i < sm.stages; ++i) {
+    const uint32_t q = sm.g + static_cast<uint32_t>(i);
+    const int b = static_cast<int>(q % static_cast<uint32_t>(sm.stages));
+    if (!mbar_wait_timed(&sm.ctl->full[b], (q / static_cast<uint32_t>(sm.stages)) & 1u))
+      sm.ctl->err = 1;
+  }
+  // the copies of g .. g + stages - 1 were the last phases of the buffers;
+  // the next open numbers its segments from there
+  return sm.g + static_cast<uint32_t>(sm.stages);
+}
+
+// One sweep over a streamed table: the segments in order, each waited for,
+// evaluated from its buffer, and released by the last warp to finish it,
+// which issues the copy `stages` segments ahead into the freed buffer.
+template <bool kTrack>
+__device__ __forceinline__ void sweep_rows_streamed(const Sweep& w, const Team& tm, Flags& f,
+                                                    Streamer& sm) {
+  const Tab& tb = w.tb;
+  for (int j = 0; j < sm.n_seg; ++j, ++sm.g) {
+    const uint32_t q = sm.g;
+    const int b = static_cast<int>(q % static_cast<uint32_t>(sm.stages));
+    const StreamSeg s = sm.seg[j];
+    const bool ready =
+        mbar_wait_timed(&sm.ctl->full[b], (q / static_cast<uint32_t>(sm.stages)) & 1u);
+    if (!ready) {
+      sm.ctl->err = 1;
+    } else {
+      const uint8_t* B = sm.buf + static_cast<size_t>(b) * kStreamChunk;
+      switch (s.kind) {
+        case kSegPairs: {
+          const uint4* R = reinterpret_cast<const uint4*>(B);
+          for (int i = tm.tid; i < s.count; i += tm.nthr) eval_reified_pair<kTrack>(w, R[i], f);
+          break;
+        }
+        case kSegSingles: {
+          const uint2* R = reinterpret_cast<const uint2*>(B);
+          for (int i = tm.tid; i < s.count; i += tm.nthr) eval_reified<kTrack>(w, R[i], f);
+          break;
+        }
+        case kSegTemporal: {
+          const uint2* R = reinterpret_cast<const uint2*>(B);
+          for (int i = tm.tid; i < s.count; i += tm.nthr) eval_temporal<kTrack>(w, R[i], f);
+          break;
+        }
+        case kSegShort: {
+          const uint32_t* T = reinterpret_cast<const uint32_t*>(B);
+          for (int i = tm.tid; i < s.count; i += tm.nthr) {
+            const int r = s.first + i;
+            if (skip_linear_short<kTrack>(w, r, f)) continue;
+            const int4 h = tb.lin[r];
+            eval_linear_thread_at<kTrack>(w, h, T + (h.y - s.term_base), f);
+          }
+          break;
+        }
+        default: {  // long rows: terms in the buffer, or in global memory
+          const bool here = s.kind == kSegLong;
+          const uint32_t* T = here ? reinterpret_cast<const uint32_t*>(B) : tb.terms_long;
+          const int base = here ? s.term_base : 0;
+          for (int i = tm.warp; i < s.count; i += tm.nwarps) {
+            const int r = s.first + i;
+            if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
+            const int4 h = tb.lin_long[r];
+            eval_linear_warp_at<kTrack>(w, h, T + (h.y - base), tm.lane, f);
+          }
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    if (tm.lane == 0) {
+      __threadfence_block();  // the warp's reads of the buffer come before its release
+      const uint32_t old = atomicAdd(&sm.ctl->done[b], 1u);
+      if (old + 1u == static_cast<uint32_t>(tm.nwarps)) {  // last warp: recycle the buffer
+        atomicExch(&sm.ctl->done[b], 0u);
+        stream_issue(sm, q + static_cast<uint32_t>(sm.stages));
+      }
+    }
+  }
 }
 
 // Per-team scalars of the fixed point (shared memory): failure flag and the
@@ -553,10 +841,13 @@ __device__ __forceinline__ void count_sweeps(const Tab& tb, const Team& tm, FixC
 // or the change buffers before the next team barrier after this returns.
 // Team-uniform return value; fc->evals / fc->bytes are valid after return
 // for the team's thread 0 (for every thread after the next team barrier).
-template <bool kTrack>
+// kStream: the table is read from global memory in segments through the
+// team's stream *sm (otherwise rows are read where tb points).  A stream that
+// lost a copy ends the loop with kError.
+template <bool kTrack, bool kStream = false>
 __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team& tm, FixCtrl* fc,
                                              const Track& tk, bool full, int max_iter,
-                                             int& iters) {
+                                             int& iters, Streamer* sm = nullptr) {
   int it = 0;
   for (;;) {
     const int cur = it % 3, prv = (it + 2) % 3, nxt = (it + 1) % 3;
@@ -566,7 +857,10 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
     }
     const Sweep w{tb, st, tk, cur, tk.chg + prv * tk.W, tk.dl + prv * tk.WL, full || !kTrack};
     Flags f{false, false, 0, 0};
-    sweep_rows<kTrack>(w, tm, f);
+    if (kStream)
+      sweep_rows_streamed<kTrack>(w, tm, f, *sm);
+    else
+      sweep_rows<kTrack>(w, tm, f);
     if (kTrack) {  // rows skipped vary: count what ran
       const int ev = __reduce_add_sync(0xffffffffu, f.evals);
       const int by = __reduce_add_sync(0xffffffffu, f.bytes);
@@ -579,6 +873,11 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
     ++it;
     full = false;
     const bool any = team_bar_or(tm.bar, tm.nthr, f.ch || f.fl);
+    if (kStream && ld_relaxed(&sm->ctl->err)) {
+      iters = it;
+      count_sweeps<kTrack>(tb, tm, fc, it);
+      return kError;
+    }
     if (ld_relaxed(&fc->fail)) {
       iters = it;
       count_sweeps<kTrack>(tb, tm, fc, it);
@@ -614,51 +913,6 @@ __device__ __forceinline__ void track_clear02(const Track& tk, const Team& tm) {
 }
 
 // ------------------------------------------------ bulk copy of the table image
-
-__device__ __forceinline__ void mbar_init(uint64_t* mbar, int count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// 1-D TMA bulk copy global -> shared, completing `bytes` on the mbarrier.
-// dst, src 16-byte aligned; bytes a multiple of 16.
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
-                                              uint64_t* mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(mbar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase: true when the phase completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity, int max_tries) {
-  for (int i = 0; i < max_tries; ++i)
-    if (mbar_try_wait(mbar, parity)) return true;
-  return false;
-}
 
 // Copy the table image into shared memory with TMA bulk copies issued by
 // thread 0 of the CTA; every thread waits (bounded) for completion.  Must be
