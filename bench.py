@@ -225,7 +225,7 @@ class ClockSampler:
 
 def explicit_launch(args):
     return bool(args.team or args.teams or args.ctas_per_sm or args.skip_stable
-                or args.no_stream_table)
+                or args.stream_table)
 
 
 def launch_desc(args):
@@ -233,7 +233,7 @@ def launch_desc(args):
         return "library default"
     return {"team_threads": args.team, "teams_per_cta": args.teams,
             "ctas_per_sm": args.ctas_per_sm, "skip_stable": bool(args.skip_stable),
-            "stream_table": not args.no_stream_table}
+            "stream_table": bool(args.stream_table)}
 
 
 KERNEL_SOURCES = ("paper_2207_12116_gb300/csrc/k_propagate.cuh",
@@ -365,7 +365,7 @@ def run_gpu(args):
     cfg = None
     if explicit_launch(args):
         cfg = pccp.launch_config(args.team, args.teams, args.ctas_per_sm, 0, args.skip_stable,
-                                 not args.no_stream_table)
+                                 args.stream_table)
 
     def prepare():
         lb.copy_(pristine_lb)
@@ -504,14 +504,12 @@ def run_search_only(args):
     print(json.dumps(search_bench(pccp, cpu=False)), flush=True)
 
 
-def run_learned(args):
-    """Learned branching against plain first-fail on 64 seeded 60-task models
-    (one persistent launch each, same limits, same GPU).  The policy is
-    trained first on nodes of the 8-task and 30-task families."""
-    import torch
+def train_policy(args):
+    """A learned-branching policy trained on nodes of the 8-task and 30-task
+    families (strong-branching probes blended with first-fail); returns
+    (policy, training summary)."""
     import paper_2207_12116_gb300 as pccp
     from paper_2207_12116_gb300 import learn
-    torch.cuda.set_device(0)
     t0 = time.perf_counter()
     train_insts = [config_instance("tiny8", s) for s in range(64)] + \
                   [config_instance("j30", s) for s in range(16)]
@@ -519,7 +517,20 @@ def run_learned(args):
     pol = pccp.Policy.random(0)
     losses = learn.train(pol, data, epochs=args.learned_epochs, groups_per_batch=256, lr=2e-3)
     acc = learn.ranking_accuracy(pol, data)
-    t_train = time.perf_counter() - t0
+    return pol, {"groups": int(data["group_off"].numel() - 1),
+                 "rows": int(data["features"].shape[0]), "epochs": args.learned_epochs,
+                 "loss_first_last": [losses[0], losses[-1]], "probe_top1_accuracy": acc,
+                 "seconds": time.perf_counter() - t0}
+
+
+def run_learned(args):
+    """Learned branching against plain first-fail on 64 seeded 60-task models
+    (one persistent launch each, same limits, same GPU).  The policy is
+    trained first on nodes of the 8-task and 30-task families."""
+    import torch
+    import paper_2207_12116_gb300 as pccp
+    torch.cuda.set_device(0)
+    pol, training = train_policy(args)
     models = [pccp.Model.from_rcpsp(config_instance("j60", 1000 + s)) for s in range(64)]
     out = {}
     for name, kw in (("first_fail", {"strategy": pccp.PCCP_FIRST_FAIL}),
@@ -555,10 +566,7 @@ def run_learned(args):
                              for k, v in proofs.items()},
             "workload": f"64 seeded 60-task 4-resource models, one launch per strategy, "
                         f"{args.learned_nodes} nodes and {args.learned_ms} ms per model",
-            "training": {"groups": int(data["group_off"].numel() - 1),
-                         "rows": int(data["features"].shape[0]), "epochs": args.learned_epochs,
-                         "loss_first_last": [losses[0], losses[-1]],
-                         "probe_top1_accuracy": acc, "seconds": t_train},
+            "training": training,
             "first_fail": {k: v for k, v in out["first_fail"].items() if k != "best_makespans"},
             "learned": {k: v for k, v in out["learned"].items() if k != "best_makespans"},
             "learned_better_equal_worse": [sum(b < a for a, b in both), sum(b == a for a, b in both),
@@ -569,8 +577,10 @@ def run_learned(args):
 def run_large(args):
     """120-task models (14,521 variables, ~570 KB table read from global
     memory) solved in one persistent launch, one 1024-thread team per model,
-    each model stopped after --large-ms; reports nodes/s, the bytes the row
-    evaluations read per second and the best makespans found."""
+    each model stopped after a time limit.  For every strategy asked for
+    (first-fail, and the learned policy trained as in --learned) and every
+    limit in --large-limits: nodes/s, the bytes the row evaluations read per
+    second and the best makespans found (best makespan against time)."""
     import torch
     import paper_2207_12116_gb300 as pccp
     torch.cuda.set_device(0)
@@ -582,29 +592,43 @@ def run_large(args):
     # memory through L1/L2 at this size): T 12 B, Rf 16 B, L 12 B + 8 B/term
     table_per_row = (12 * info.n_temporal + 16 * info.n_reified + 12 * info.n_linear
                      + 8 * info.n_terms) / models[0].rows
-    strategy = pccp.PCCP_FIRST_FAIL
-    t0 = time.perf_counter()
-    res = pccp.solve_batch(models, strategy=strategy, time_limit_ms=args.large_ms,
-                           stream_table=not args.no_stream_table)
-    wall = time.perf_counter() - t0
-    ms = res[0]["elapsed_ms"]
-    nodes = sum(r["nodes"] for r in res)
-    rows = sum(r["rows_evaluated"] for r in res)
-    found = [r["objective"] for r in res if r["has_solution"]]
+    limits = [int(x) for x in args.large_limits.split(",")] if args.large_limits else [args.large_ms]
+    strategies = [("first_fail", {"strategy": pccp.PCCP_FIRST_FAIL})]
+    training = None
+    if args.large_learned:
+        pol, training = train_policy(args)
+        strategies.append(("learned", {"strategy": pccp.PCCP_LEARNED, "policy": pol}))
+    runs = []
+    for name, kw in strategies:
+        for lim in limits:
+            t0 = time.perf_counter()
+            res = pccp.solve_batch(models, time_limit_ms=lim, stream_table=args.stream_table,
+                                   **kw)
+            wall = time.perf_counter() - t0
+            ms = res[0]["elapsed_ms"]
+            nodes = sum(r["nodes"] for r in res)
+            rows = sum(r["rows_evaluated"] for r in res)
+            found = [r["objective"] for r in res if r["has_solution"]]
+            runs.append({"strategy": name, "limit_ms": lim, "kernel_ms": ms, "wall_s": wall,
+                         "nodes": nodes, "nodes_per_s": nodes / (ms / 1000),
+                         "propagator_evals_per_s": rows / (ms / 1000),
+                         "row_bytes_per_s": rows * bytes_per_row / (ms / 1000),
+                         "table_gbs": rows * table_per_row / (ms / 1000) / 1e9,
+                         "models_with_solution": len(found),
+                         "mean_best_makespan": float(np.mean(found)) if found else None})
+    first = runs[0]
     line = {"metric": "search nodes/s, best makespan under a time limit (120-task models)",
-            "workload": f"{args.large_models} seeded 120-task 4-resource models, first-fail, "
-                        f"one launch, {args.large_ms} ms per model",
-            "nodes_per_s": nodes / (ms / 1000), "propagator_evals_per_s": rows / (ms / 1000),
-            "row_bytes_per_s": rows * bytes_per_row / (ms / 1000),
-            "kernel_ms": ms, "wall_s": wall, "nodes": nodes,
-            "models_with_solution": len(found),
-            "mean_best_makespan": float(np.mean(found)) if found else None,
-            "stream_table": not args.no_stream_table}
-    tbs = rows * table_per_row / (ms / 1000) / 1e9
-    line["table_stream"] = {"achieved_gbs": tbs, "table_bytes": info.table_bytes}
+            "workload": f"{args.large_models} seeded 120-task 4-resource models, one launch per "
+                        f"strategy and limit, one 1024-thread team per model",
+            **{k: first[k] for k in ("nodes_per_s", "propagator_evals_per_s", "row_bytes_per_s",
+                                     "kernel_ms", "wall_s", "nodes", "models_with_solution",
+                                     "mean_best_makespan")},
+            "runs": runs, "training": training, "stream_table": bool(args.stream_table)}
+    line["table_stream"] = {"achieved_gbs": first["table_gbs"], "table_bytes": info.table_bytes}
     if not args.no_probes:
         l2 = pccp.roofline_probes()["l2_read"]
-        line["table_stream"].update({"l2_probe_gbs": l2["gbs"], "frac_of_l2_probe": tbs / l2["gbs"]})
+        line["table_stream"].update({"l2_probe_gbs": l2["gbs"],
+                                     "frac_of_l2_probe": first["table_gbs"] / l2["gbs"]})
     print(json.dumps(line), flush=True)
 
 
@@ -631,9 +655,14 @@ def main():
     ap.add_argument("--large", action="store_true",
                     help="120-task models in one launch (own JSON line)")
     ap.add_argument("--large-models", type=int, default=1024)
-    ap.add_argument("--no-stream-table", action="store_true",
-                    help="read tables too large for shared memory in place (no TMA streaming)")
+    ap.add_argument("--stream-table", action="store_true",
+                    help="stream tables too large for shared memory through TMA bulk-copy "
+                         "rings (default: read in place)")
     ap.add_argument("--large-ms", type=int, default=7000)
+    ap.add_argument("--large-limits", default="",
+                    help="comma-separated time limits (ms) for a best-makespan-vs-time curve")
+    ap.add_argument("--large-learned", action="store_true",
+                    help="also run the learned policy (trained first, as in --learned)")
     ap.add_argument("--search-only", action="store_true",
                     help="small search leg only (64 models x 500 nodes; parallel runs "
                          "stopped after 2,000,000 nodes)")

@@ -150,10 +150,10 @@ typedef struct {
   int32_t skip_stable;    /* 1: re-run a row only after one of its variables changed
                              (change bitmaps per team; Sec. 6); 0: the eventless loop
                              of Sec. 5.  Same fixed point either way. */
-  int32_t stream_table;   /* tables too large for shared memory: 0 stream them through
+  int32_t stream_table;   /* tables too large for shared memory: 0 read rows in place
+                             (through L1/L2); 1 stream them through a ring of
                              shared-memory buffers by TMA bulk copies, segment by
-                             segment, every sweep; -1 read rows in place (L1/L2).
-                             Same fixed point either way. */
+                             segment, every sweep.  Same fixed point either way. */
 } pccp_launch_config;
 
 /* pccp_propagate with an explicit launch shape (cfg may be NULL) and an

@@ -219,11 +219,11 @@ def _stream_ptr(stream):
 
 
 def launch_config(team_threads=0, teams_per_cta=0, ctas_per_sm=0, max_iterations=0,
-                  skip_stable=False, stream_table=True):
-    """stream_table=False reads a table too large for shared memory in place
-    instead of streaming it through shared-memory buffers."""
+                  skip_stable=False, stream_table=False):
+    """stream_table=True streams a table too large for shared memory through
+    shared-memory buffers (TMA bulk copies) instead of reading it in place."""
     return _abi.pccp_launch_config(team_threads, teams_per_cta, ctas_per_sm, max_iterations,
-                                   int(bool(skip_stable)), 0 if stream_table else -1)
+                                   int(bool(skip_stable)), int(bool(stream_table)))
 
 
 def propagate(model: Model, lb, ub, status=None, iterations=None, config=None, stream=None,
@@ -265,10 +265,10 @@ def propagate_host(model: Model, lb, ub, device="cuda", config=None, stream=None
 
 
 def _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
-          skip_stable=False, policy=None, stream_table=True):
+          skip_stable=False, policy=None, stream_table=False):
     return _abi.pccp_solve_opts(strategy, mode, int(bool(deterministic)), obj_ub, node_limit,
                                 time_limit_ms, threads, blocks, int(bool(skip_stable)),
-                                0 if stream_table else -1,
+                                int(bool(stream_table)),
                                 policy.handle if policy is not None else None)
 
 
@@ -283,7 +283,7 @@ def _result_dict(r, w):
 
 def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, deterministic=True,
           obj_ub=INT32_MAX, node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None,
-          skip_stable=False, policy=None, stream_table=True):
+          skip_stable=False, policy=None, stream_table=False):
     o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
               skip_stable, policy, stream_table)
     w = np.zeros(model.n_vars, dtype=np.int32)
@@ -296,7 +296,7 @@ def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, determini
 
 def solve_batch(models, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
                 node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None, noalloc=False,
-                skip_stable=False, policy=None, stream_table=True):
+                skip_stable=False, policy=None, stream_table=False):
     """Solve many models in one launch.  noalloc=True uses the allocation-free
     entry point (fixed device scratch; see include/pccp.h)."""
     o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, threads, blocks,

@@ -692,10 +692,10 @@ size_t solve_smem(uint32_t max_img, int max_track_words, int max_vars, int x_wor
 
 // Stream buffers per team for a table read from global memory: the most
 // (3, else 2) that fit beside `teams` teams of `per_team` bytes; 0 when the
-// table has no rows, streaming is switched off, or not even two fit.
+// table has no rows, streaming is not asked for, or not even two fit.
 int stream_stages_for(int n_seg, int stream_opt, size_t fixed, size_t per_team, int teams,
                       int smem_max) {
-  if (n_seg <= 0 || stream_opt < 0) return 0;
+  if (n_seg <= 0 || stream_opt <= 0) return 0;
   for (int s = kStreamMaxStages; s >= 2; --s)
     if (fixed + static_cast<size_t>(teams) * (per_team + stream_bytes(s)) <=
         static_cast<size_t>(smem_max))

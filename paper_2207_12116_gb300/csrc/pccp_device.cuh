@@ -628,7 +628,7 @@ struct StreamCtl {
   int32_t err;                      // a wait gave up (set by any thread)
   int32_t pad;
 };
-static_assert(sizeof(StreamCtl) == 48, "stream control words");
+static_assert(sizeof(StreamCtl) <= 128, "stream control words");
 constexpr int kStreamCtlBytes = 128;  // keeps the buffers 128-byte aligned
 
 __host__ __device__ __forceinline__ size_t stream_bytes(int stages) {

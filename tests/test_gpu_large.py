@@ -51,7 +51,8 @@ def test_j120_batch_switches_streams_between_models():
     """One CTA searches several 120-task models in turn: each model's stream
     is closed and the next one opened on the same buffers."""
     insts = [config_instance("j120", s) for s in (3, 4, 5)]
-    res = pccp.solve_batch([pccp.Model.from_rcpsp(i) for i in insts], node_limit=6, blocks=1)
+    res = pccp.solve_batch([pccp.Model.from_rcpsp(i) for i in insts], node_limit=6, blocks=1,
+                           stream_table=True)
     for inst, r in zip(insts, res):
         o = oracle.solve(rcpsp_model(inst), node_limit=6)
         assert (r["nodes"], r["fails"], r["solutions"]) == (o["nodes"], o["fails"], o["solutions"])
