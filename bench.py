@@ -238,7 +238,9 @@ def launch_desc(args):
 
 KERNEL_SOURCES = ("paper_2207_12116_gb300/csrc/k_propagate.cuh",
                   "paper_2207_12116_gb300/csrc/pccp_device.cuh")
-PROFILE = "profiles/k_propagate_j30_batch.md"
+def profile_path():
+    """The committed ncu summary of the propagation workload being run."""
+    return f"profiles/k_propagate_{FAMILY}_batch.md"
 
 
 def kernel_hash():
@@ -253,7 +255,7 @@ def recorded_traffic():
     """DRAM bytes per launch of k_propagate from the committed ncu summary,
     or None when the kernel sources changed since that capture."""
     try:
-        text = open(os.path.join(ROOT, PROFILE)).read()
+        text = open(os.path.join(ROOT, profile_path())).read()
     except OSError:
         return None, None
     rec = {}
@@ -263,8 +265,10 @@ def recorded_traffic():
             rec[k.strip()] = v.strip()
     if rec.get("kernel_sha") != kernel_hash():
         return None, "kernel changed since the committed ncu capture"
+    if rec.get("nodes", str(N_NODES)) != str(N_NODES):
+        return None, "the committed ncu capture is of another batch size"
     try:
-        return int(rec["dram_bytes_per_launch"]), PROFILE
+        return int(rec["dram_bytes_per_launch"]), profile_path()
     except (KeyError, ValueError):
         return None, None
 

@@ -116,6 +116,9 @@ typedef struct {
   int32_t max_store_vars;   /* largest n_vars a single CTA can stage */
   int32_t n_segments;       /* byte ranges of whole rows (<= 32 KB each) that one sweep
                                streams when the table is read from global memory */
+  int32_t reordered;        /* 1: the library keeps the variables in shared memory in
+                               its own order (chosen at create for fewer bank conflicts;
+                               every array the caller sees stays in the caller's order) */
 } pccp_model_info;
 
 int pccp_model_get_info(const pccp_model* model, pccp_model_info* info);

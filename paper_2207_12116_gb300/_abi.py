@@ -45,7 +45,7 @@ class pccp_model_desc(ctypes.Structure):
 class pccp_model_info(ctypes.Structure):
     _fields_ = [("n_vars", I32), ("n_temporal", I32), ("n_linear", I32), ("n_terms", I32),
                 ("n_reified", I32), ("table_bytes", I32), ("bytes_per_sweep", I64),
-                ("max_store_vars", I32), ("n_segments", I32)]
+                ("max_store_vars", I32), ("n_segments", I32), ("reordered", I32)]
 
 
 class pccp_launch_config(ctypes.Structure):

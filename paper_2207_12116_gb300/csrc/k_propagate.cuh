@@ -30,6 +30,7 @@ struct PropArgs {
   int track_words;
   int table_global;   // 1: rows are read from the device image (too big for shared memory)
   int stream_stages;  // table_global: buffers of each team's stream (kStream kernels)
+  int reordered;      // 1: st uses the library's variable order (internal_of after the root)
 };
 
 // Per-team scalars of k_propagate (shared memory).
@@ -77,6 +78,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   const Track tk = make_track(track_base + static_cast<size_t>(tw16) * team_id, tb.n_vars,
                               tb.n_lin + tb.n_lin_long);
   const int nv = a.n_vars;
+  // the library's index of each of the caller's variables (after the root)
+  const int32_t* internal_of = reinterpret_cast<const int32_t*>(a.root + nv);
   Streamer stream;
   if (kStream)  // published by the barrier at the top of the store loop
     stream = stream_open(smem + stream_region * team_id, a.stream_stages, tb, a.image, tm, 0u);
@@ -97,12 +100,14 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
       }
       continue;
     }
+    // stores are in the caller's variable order, st in the library's
     int32_t* lbs = a.lb + static_cast<size_t>(s) * nv;
     int32_t* ubs = a.ub + static_cast<size_t>(s) * nv;
     bool empty = false;
-    for (int v = tm.tid; v < nv; v += tm.nthr) {
+    for (int x = tm.tid; x < nv; x += tm.nthr) {
+      const int v = a.reordered ? __ldg(internal_of + x) : x;
       const int2 r = __ldg(a.root + v);
-      const int l = max(lbs[v], r.x), u = min(ubs[v], r.y);
+      const int l = max(lbs[x], r.x), u = min(ubs[x], r.y);
       st[v] = make_int2(l, u);
       empty |= l > u;
     }
@@ -117,10 +122,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
     if (!any_empty)
       status = team_fixpoint<kTrack, kStream>(tb, st, tm, &ctrl->fc, tk, true, a.max_iter, it,
                                               &stream);
-    for (int v = tm.tid; v < nv; v += tm.nthr) {
-      const int2 D = st[v];
-      lbs[v] = D.x;
-      ubs[v] = D.y;
+    for (int x = tm.tid; x < nv; x += tm.nthr) {
+      const int2 D = st[a.reordered ? __ldg(internal_of + x) : x];
+      lbs[x] = D.x;
+      ubs[x] = D.y;
     }
     if (tm.tid == 0) {
       a.status[s] = status;

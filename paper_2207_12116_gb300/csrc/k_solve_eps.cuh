@@ -185,8 +185,10 @@ __device__ __forceinline__ void eps_solution(const Tab& tb, int2* st, const Team
   }
   team_bar(tm.bar, tm.nthr);
   if (sc->record) {
+    // in the caller's variable order (internal_of after the root)
     int32_t* w = a.witness + static_cast<size_t>(team_gid) * a.n_vars;
-    for (int v = tm.tid; v < a.n_vars; v += tm.nthr) w[v] = st[v].x;
+    const int32_t* internal_of = reinterpret_cast<const int32_t*>(a.root + a.n_vars);
+    for (int x = tm.tid; x < a.n_vars; x += tm.nthr) w[x] = st[__ldg(internal_of + x)].x;
   }
 }
 

@@ -211,8 +211,10 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
           sc->record = record;
         }
         team_bar(tm.bar, tm.nthr);  // N3
-        if (sc->record)
-          for (int v = tm.tid; v < nv; v += tm.nthr) witness[v] = st[v].x;
+        if (sc->record) {  // in the caller's variable order (internal_of after the root)
+          const int32_t* internal_of = reinterpret_cast<const int32_t*>(root + nv);
+          for (int x = tm.tid; x < nv; x += tm.nthr) witness[x] = st[__ldg(internal_of + x)].x;
+        }
       } else {
         backtrack = false;
         if (tm.tid == 0) {
@@ -363,6 +365,7 @@ struct pccp_model {
   int device;
   int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective;
   int32_t n_seg;  // stream segments of the table
+  int32_t reordered;  // 1: shared-memory stores use the library's variable order
   uint32_t image_bytes;
   int64_t bytes_per_sweep;
   int32_t max_iter;  // every changing iteration narrows some bound by >= 1
@@ -373,6 +376,172 @@ struct pccp_model {
 namespace {
 
 int64_t iabs64(int64_t x) { return x < 0 ? -x : x; }
+
+// Reified rows {x | y << 16, b | d << 16} (sorted by b) that pair up: rows
+// over the same two variables with the roles swapped, matched first come
+// first served; returns (first row, second row) in the order of the first.
+std::vector<std::pair<size_t, size_t>> reified_pairs(const std::vector<uint2>& RF) {
+  std::vector<std::pair<size_t, size_t>> out;
+  std::unordered_map<uint32_t, std::vector<size_t>> waiting;  // (x | y << 16) -> rows
+  std::vector<char> used(RF.size(), 0);
+  for (size_t r = 0; r < RF.size(); ++r) waiting[RF[r].x].push_back(r);
+  for (size_t r = 0; r < RF.size(); ++r) {
+    if (used[r]) continue;
+    const uint32_t x = RF[r].x & 0xffffu, y = RF[r].x >> 16;
+    if (x == y) continue;
+    auto it = waiting.find(y | (x << 16));
+    if (it == waiting.end()) continue;
+    for (size_t q : it->second) {
+      if (used[q] || q == r) continue;
+      used[r] = used[q] = 1;
+      out.emplace_back(r, q);
+      break;
+    }
+  }
+  return out;
+}
+
+// Shared-memory wavefronts of one warp's 8-byte interval loads of the
+// variables vars[0..n) (one per lane, n <= 32) under the order iof: per
+// half-warp (128 bytes a wavefront), the largest number of distinct words
+// that fall in one of the 32 four-byte banks.
+int warp_wavefronts(const int32_t* vars, int n, const std::vector<int32_t>& iof) {
+  int total = 0;
+  for (int h = 0; h < n; h += 16) {
+    uint32_t words[32];
+    int nw = 0;
+    for (int l = h; l < std::min(n, h + 16); ++l) {
+      const uint32_t w = 2u * static_cast<uint32_t>(iof[vars[l]]);
+      words[nw++] = w;
+      words[nw++] = w + 1;
+    }
+    int worst = 0;
+    for (int b = 0; b < 32; ++b) {
+      int distinct = 0;
+      for (int i = 0; i < nw; ++i) {
+        if (words[i] % 32 != static_cast<uint32_t>(b)) continue;
+        bool seen = false;
+        for (int j = 0; j < i; ++j) seen = seen || words[j] == words[i];
+        distinct += seen ? 0 : 1;
+      }
+      worst = std::max(worst, distinct);
+    }
+    total += worst;
+  }
+  return total;
+}
+
+// Wavefronts of the interval loads of one sweep in the kernels' row order
+// (reified pairs and single rows by thread, short linear rows by thread in
+// tiles of 32 sorted longest first, long rows by warp; temporal rows are few
+// and left out), under the order iof.
+int64_t sweep_wavefronts(const pccp_model_desc* d, const std::vector<uint2>& RF,
+                         const std::vector<std::pair<size_t, size_t>>& pairs,
+                         const std::vector<int32_t>& iof) {
+  int64_t total = 0;
+  int32_t lanes[4][32];
+  for (size_t g = 0; g < pairs.size(); g += 32) {
+    const int n = static_cast<int>(std::min<size_t>(32, pairs.size() - g));
+    for (int l = 0; l < n; ++l) {
+      const uint2 r1 = RF[pairs[g + l].first], r2 = RF[pairs[g + l].second];
+      lanes[0][l] = static_cast<int32_t>(r1.x & 0xffffu);
+      lanes[1][l] = static_cast<int32_t>(r1.x >> 16);
+      lanes[2][l] = static_cast<int32_t>(r1.y & 0xffffu);
+      lanes[3][l] = static_cast<int32_t>(r2.y & 0xffffu);
+    }
+    for (int k = 0; k < 4; ++k) total += warp_wavefronts(lanes[k], n, iof);
+  }
+  if (d->n_linear <= 0) return total;
+  std::vector<std::vector<int32_t>> rows;
+  for (int32_t i = 0; i < d->n_linear; ++i) {
+    std::vector<int32_t> t;
+    for (int32_t k = d->linear_off[i]; k < d->linear_off[i + 1]; ++k)
+      if (d->term_coef[k] != 0) t.push_back(d->term_var[k]);
+    rows.push_back(std::move(t));
+  }
+  std::vector<const std::vector<int32_t>*> shorts;
+  for (const auto& r : rows) {
+    if (r.size() <= static_cast<size_t>(kShortRow)) {
+      shorts.push_back(&r);
+    } else {
+      for (size_t k = 0; k < r.size(); k += 32)
+        total += warp_wavefronts(r.data() + k, static_cast<int>(std::min<size_t>(32, r.size() - k)),
+                                 iof);
+    }
+  }
+  std::stable_sort(shorts.begin(), shorts.end(),
+                   [](const std::vector<int32_t>* p, const std::vector<int32_t>* q) {
+                     return p->size() > q->size();
+                   });
+  for (size_t t0 = 0; t0 < shorts.size(); t0 += 32) {
+    const size_t t1 = std::min(shorts.size(), t0 + 32);
+    for (size_t k = 0; k < shorts[t0]->size(); ++k) {
+      int n = 0;
+      for (size_t r = t0; r < t1; ++r)
+        if (k < shorts[r]->size()) lanes[0][n++] = (*shorts[r])[k];
+      total += warp_wavefronts(lanes[0], n, iof);
+    }
+  }
+  return total;
+}
+
+// The library's own numbering of a model's variables (internal_of[user]).
+// Stores are kept in shared memory in this order.  Candidates: the caller's
+// order, and the pair-block order -- every variable that is the Boolean of no
+// reified pair first, in the caller's order, then the first Booleans of the
+// pairs in pair order, then the second ones, so that neighbouring lanes that
+// evaluate neighbouring pairs load neighbouring words (in the caller's order
+// one of the two Booleans may sit a model's width apart, every lane on the
+// same banks; a linear row over one column of a matrix of Booleans strides
+// by its width too).  The one whose sweep has fewer shared-memory wavefronts
+// (sweep_wavefronts) is kept.  The caller's order stays the interface:
+// stores are read and written, and witnesses written, through this map.
+// Identity when the model has an index out of range (validation reports it).
+std::vector<int32_t> internal_order(const pccp_model_desc* d) {
+  const int32_t nv = d->n_vars;
+  std::vector<int32_t> iof(nv > 0 ? nv : 0);
+  for (int32_t v = 0; v < nv; ++v) iof[v] = v;
+  if (nv <= 0 || nv > 65535 || d->n_reified <= 0 || !d->reified) return iof;
+  if (d->n_linear < 0 || (d->n_linear > 0 && (!d->linear_off || !d->term_var || !d->term_coef)))
+    return iof;
+  for (int32_t i = 0; i < d->n_linear; ++i)
+    if (d->linear_off[0] != 0 || d->linear_off[i + 1] < d->linear_off[i]) return iof;
+  for (int32_t k = 0; d->n_linear > 0 && k < d->linear_off[d->n_linear]; ++k)
+    if (d->term_var[k] < 0 || d->term_var[k] >= nv) return iof;
+  std::vector<uint2> RF;
+  for (int32_t i = 0; i < d->n_reified; ++i) {
+    const int32_t b = d->reified[4 * i], x = d->reified[4 * i + 1], y = d->reified[4 * i + 2];
+    if (b < 0 || b >= nv || x < 0 || x >= nv || y < 0 || y >= nv) return iof;
+    RF.push_back(make_uint2(static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 16),
+                            static_cast<uint32_t>(b)));
+  }
+  std::stable_sort(RF.begin(), RF.end(),
+                   [](const uint2& p, const uint2& q) { return (p.y & 0xffffu) < (q.y & 0xffffu); });
+  const auto pairs = reified_pairs(RF);
+  if (pairs.empty()) return iof;
+  std::vector<int32_t> block(nv, 0);  // 0 rest, 1 first Booleans, 2 second ones
+  std::vector<int32_t> first, second;
+  for (const auto& pq : pairs) {
+    const int32_t b1 = static_cast<int32_t>(RF[pq.first].y & 0xffffu);
+    const int32_t b2 = static_cast<int32_t>(RF[pq.second].y & 0xffffu);
+    if (block[b1] == 0) {
+      block[b1] = 1;
+      first.push_back(b1);
+    }
+    if (block[b2] == 0) {
+      block[b2] = 2;
+      second.push_back(b2);
+    }
+  }
+  std::vector<int32_t> blocks(nv);
+  int32_t next = 0;
+  for (int32_t v = 0; v < nv; ++v)
+    if (block[v] == 0) blocks[v] = next++;
+  for (int32_t v : first) blocks[v] = next++;
+  for (int32_t v : second) blocks[v] = next++;
+  return sweep_wavefronts(d, RF, pairs, blocks) < sweep_wavefronts(d, RF, pairs, iof) ? blocks
+                                                                                       : iof;
+}
 
 int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   if (!d) return PCCP_ERR_INVALID;
@@ -434,21 +603,10 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   std::vector<uint4> RFP;
   {
     std::vector<uint2> single;
-    std::unordered_map<uint32_t, std::vector<size_t>> waiting;  // (x | y << 16) -> rows
     std::vector<char> used(RF.size(), 0);
-    for (size_t r = 0; r < RF.size(); ++r) waiting[RF[r].x].push_back(r);
-    for (size_t r = 0; r < RF.size(); ++r) {
-      if (used[r]) continue;
-      const uint32_t x = RF[r].x & 0xffffu, y = RF[r].x >> 16;
-      if (x == y) continue;
-      auto it = waiting.find(y | (x << 16));
-      if (it == waiting.end()) continue;
-      for (size_t q : it->second) {
-        if (used[q] || q == r) continue;
-        used[r] = used[q] = 1;
-        RFP.push_back(make_uint4(RF[r].x, RF[r].y, RF[q].y, 0u));
-        break;
-      }
+    for (const auto& pq : reified_pairs(RF)) {
+      used[pq.first] = used[pq.second] = 1;
+      RFP.push_back(make_uint4(RF[pq.first].x, RF[pq.first].y, RF[pq.second].y, 0u));
     }
     for (size_t r = 0; r < RF.size(); ++r)
       if (!used[r]) single.push_back(RF[r]);
@@ -863,9 +1021,59 @@ const char* pccp_error_string(int code) {
   }
 }
 
-int pccp_model_create(const pccp_model_desc* desc, pccp_model** out) {
+int pccp_model_create(const pccp_model_desc* desc_user, pccp_model** out) {
   if (!out) return PCCP_ERR_INVALID;
   *out = nullptr;
+  if (!desc_user) return PCCP_ERR_INVALID;
+  // the model in the library's variable order (internal_order)
+  const std::vector<int32_t> iof = internal_order(desc_user);
+  const int32_t nv_user = desc_user->n_vars > 0 ? desc_user->n_vars : 0;
+  std::vector<int32_t> uof(nv_user);
+  for (int32_t v = 0; v < nv_user; ++v) uof[iof[v]] = v;
+  auto map_var = [&iof, nv_user](int32_t v) { return v >= 0 && v < nv_user ? iof[v] : v; };
+  std::vector<int32_t> lb0, ub0, tmp, rf, tv, br;
+  pccp_model_desc dd = *desc_user;
+  if (desc_user->lb0 && desc_user->ub0) {
+    lb0.resize(nv_user);
+    ub0.resize(nv_user);
+    for (int32_t v = 0; v < nv_user; ++v) {
+      lb0[iof[v]] = desc_user->lb0[v];
+      ub0[iof[v]] = desc_user->ub0[v];
+    }
+    dd.lb0 = lb0.data();
+    dd.ub0 = ub0.data();
+  }
+  if (desc_user->n_temporal > 0 && desc_user->temporal) {
+    tmp.assign(desc_user->temporal, desc_user->temporal + 3 * desc_user->n_temporal);
+    for (int32_t i = 0; i < desc_user->n_temporal; ++i) {
+      tmp[3 * i] = map_var(tmp[3 * i]);
+      tmp[3 * i + 1] = map_var(tmp[3 * i + 1]);
+    }
+    dd.temporal = tmp.data();
+  }
+  if (desc_user->n_reified > 0 && desc_user->reified) {
+    rf.assign(desc_user->reified, desc_user->reified + 4 * desc_user->n_reified);
+    for (int32_t i = 0; i < desc_user->n_reified; ++i)
+      for (int k = 0; k < 3; ++k) rf[4 * i + k] = map_var(rf[4 * i + k]);
+    dd.reified = rf.data();
+  }
+  bool offsets_ok = desc_user->n_linear > 0 && desc_user->linear_off && desc_user->term_var &&
+                    desc_user->linear_off[0] == 0;
+  for (int32_t i = 0; offsets_ok && i < desc_user->n_linear; ++i)
+    offsets_ok = desc_user->linear_off[i + 1] >= desc_user->linear_off[i];
+  if (offsets_ok) {  // else validation rejects the model before reading terms
+    const int32_t nt = desc_user->linear_off[desc_user->n_linear];
+    tv.assign(desc_user->term_var, desc_user->term_var + nt);
+    for (int32_t& v : tv) v = map_var(v);
+    dd.term_var = tv.data();
+  }
+  if (desc_user->n_branch > 0 && desc_user->branch_vars) {
+    br.assign(desc_user->branch_vars, desc_user->branch_vars + desc_user->n_branch);
+    for (int32_t& v : br) v = map_var(v);
+    dd.branch_vars = br.data();
+  }
+  dd.objective = map_var(desc_user->objective);
+  const pccp_model_desc* desc = &dd;
   Packed p;
   const int rc = validate_and_pack(desc, &p);
   if (rc != PCCP_OK) return rc;
@@ -884,14 +1092,17 @@ int pccp_model_create(const pccp_model_desc* desc, pccp_model** out) {
   m->image_bytes = static_cast<uint32_t>(p.image.size());
   m->bytes_per_sweep = p.bytes_per_sweep;
   m->n_seg = p.n_seg;
+  m->reordered = 0;
+  for (int32_t v = 0; v < nv_user; ++v) m->reordered |= iof[v] != v ? 1 : 0;
   {
     // total width of the root box + 3 bounds the iterations of any store
     int64_t w = 3;
     for (int v = 0; v < p.n_vars; ++v) w += static_cast<int64_t>(desc->ub0[v]) - desc->lb0[v];
     m->max_iter = static_cast<int32_t>(std::min<int64_t>(w, kDefaultMaxIter));
   }
+  // device memory: image | root int2[n] | internal_of int32[n] | user_of int32[n]
   const size_t root_off = align16(p.image.size());
-  const size_t total = root_off + static_cast<size_t>(p.n_vars) * sizeof(int2);
+  const size_t total = root_off + static_cast<size_t>(p.n_vars) * (sizeof(int2) + 8);
   std::vector<int2> root(p.n_vars);
   for (int v = 0; v < p.n_vars; ++v) root[v] = make_int2(desc->lb0[v], desc->ub0[v]);
   if (cudaMalloc(&m->d_mem, total) != cudaSuccess) {
@@ -900,9 +1111,14 @@ int pccp_model_create(const pccp_model_desc* desc, pccp_model** out) {
     return PCCP_ERR_CUDA;
   }
   m->d_root = reinterpret_cast<int2*>(m->d_mem + root_off);
+  int32_t* d_iof = reinterpret_cast<int32_t*>(m->d_root + p.n_vars);
   if (cudaMemcpy(m->d_mem, p.image.data(), p.image.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(m->d_root, root.data(), root.size() * sizeof(int2), cudaMemcpyHostToDevice) !=
-          cudaSuccess) {
+          cudaSuccess ||
+      cudaMemcpy(d_iof, iof.data(), iof.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(d_iof + p.n_vars, uof.data(), uof.size() * sizeof(int32_t),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
     (void)cudaGetLastError();
     cudaFree(m->d_mem);
     delete m;
@@ -936,6 +1152,7 @@ int pccp_model_get_info(const pccp_model* m, pccp_model_info* info) {
   int64_t room = static_cast<int64_t>(smem_max) - m->image_bytes - 32;
   info->max_store_vars = room > 0 ? static_cast<int32_t>(std::min<int64_t>(room / 8, 65535)) : 0;
   info->n_segments = m->n_seg;
+  info->reordered = m->reordered;
   return PCCP_OK;
 }
 
@@ -972,6 +1189,7 @@ int pccp_propagate_ex(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_
   a.work = work;
   a.table_global = plan.table_global ? 1 : 0;
   a.stream_stages = plan.stages;
+  a.reordered = m->reordered;
   plan.kern<<<plan.grid, plan.team * plan.teams, plan.smem, s>>>(a);
   const cudaError_t le = cudaGetLastError();
   cudaFreeAsync(counter, s);

@@ -215,15 +215,19 @@ __global__ void k_policy_features(const uint8_t* __restrict__ image, const int2*
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<long long>(n_stores) * nb) return;
   const int s = static_cast<int>(i / nb), k = static_cast<int>(i - static_cast<long long>(s) * nb);
+  // stores are in the caller's variable order; the table and root in the
+  // library's (user_of: the caller's index of each variable, after the root)
+  const int32_t* user_of = reinterpret_cast<const int32_t*>(root + n_vars) + n_vars;
   const int v = tb.branch[k];
   const int32_t* l = lb + static_cast<size_t>(s) * n_vars;
   const int32_t* u = ub + static_cast<size_t>(s) * n_vars;
   const int2 R = root[v];
-  const int2 D = make_int2(max(l[v], R.x), min(u[v], R.y));
+  const int vu = user_of[v];
+  const int2 D = make_int2(max(l[vu], R.x), min(u[vu], R.y));
   float prog = 0.f;
   if (tb.objective >= 0) {
     const int2 RO = root[tb.objective];
-    prog = static_cast<float>(max(l[tb.objective], RO.x) - RO.x) /
+    prog = static_cast<float>(max(l[user_of[tb.objective]], RO.x) - RO.x) /
            (static_cast<float>(RO.y - RO.x) + 1.f);
   }
   uint32_t row[8];

@@ -27,6 +27,7 @@ def test_j120_propagation_bit_exact(stream_table):
     rows = pccp.rcpsp.build_rows(inst)
     m = pccp.Model.from_rows(rows)
     assert m.info.n_segments > 10
+    assert m.info.reordered == 1  # pair-block order: far fewer bank conflicts here
     om = rcpsp_model(inst)
     nodes = [[]] + draw_partial_assignments(inst.n, inst.horizon, 11, seed=21)
     lb, ub = pccp.rcpsp.node_stores(rows, nodes)

@@ -77,6 +77,7 @@ def test_long_linear_rows_and_wide_domains():
 def test_j30_nodes_bit_exact():
     inst = config_instance("j30", 0)
     m = pccp.Model.from_rcpsp(inst)
+    assert m.info.reordered == 0  # the caller's order has fewer bank conflicts here
     om = rcpsp_model(inst)
     nodes = draw_partial_assignments(inst.n, inst.horizon, 1500, seed=1)
     rows = pccp.rcpsp.build_rows(inst)
@@ -167,3 +168,29 @@ def test_edge_cases():
     chain = pccp.Model.from_lists([0] * 6, [50] * 6, temporal=[(i, i + 1, 2) for i in range(5)])
     st, *_ = run(chain, np.zeros((1, 6)), np.full((1, 6), 50), pccp.launch_config(32, 1, 0, 1))
     assert st.tolist() == [pccp.PCCP_ERROR]
+
+
+def test_store_size_limits():
+    """A store larger than shared memory is refused on the host; a store near
+    the limit (table read from global memory) is still bit-exact."""
+    big = pccp.Model([0] * 40000, [1] * 40000)
+    assert big.info.max_store_vars < 40000
+    with pytest.raises(pccp.PccpError) as e:
+        run(big, np.zeros((1, 40000)), np.ones((1, 40000)))
+    assert e.value.code == pccp.PCCP_ERR_SMEM
+    n = int(0.9 * pccp.Model([0], [1]).info.max_store_vars)
+    g = np.random.default_rng(4)
+    lb0 = [0] * n
+    ub0 = [int(v) for v in g.integers(100, 100000, n)]
+    temporal = [(i, i + 1, int(g.integers(0, 3))) for i in range(0, n - 1, 2)]
+    linear = [(int(g.integers(50, 500)), [(1, int(a)), (2, int(b)), (-1, int(c))])
+              for a, b, c in g.integers(0, n, (2000, 3))]
+    m = pccp.Model.from_lists(lb0, ub0, temporal, linear)
+    om = oracle.Model(lb0, ub0, temporal, linear, [], -1, [])
+    lb = np.tile(np.array(lb0, dtype=np.int32), (3, 1))
+    ub = np.tile(np.array(ub0, dtype=np.int32), (3, 1))
+    lb[1, ::7] = 40
+    ub[2, 1::5] = 30
+    st, glb, gub, _ = run(m, lb, ub)
+    x, f = compare_batch(om, lb, ub, st, glb, gub)
+    assert x >= 2
