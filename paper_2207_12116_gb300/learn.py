@@ -8,10 +8,14 @@ probed the way strong branching does: both children of its lower-half split
 are propagated (again by pccp_propagate, all children of a batch in one
 launch) and scored by the failures they expose and the domain reduction they
 cause.  The expert blends this probe with first-fail's preference for small
-domains (a probe alone favours splits that fail or shrink domains, which
-makes depth-first dives thrash before any assignment completes); the target
-of a node is the softmax of the expert's scores over its candidates, and the
-policy learns to rank candidates like the expert without running the probe.
+domains and its tie-break (lower branch index first): a probe alone favours
+splits that fail or shrink domains, which makes depth-first dives thrash
+before any assignment completes, and without the tie-break the many equal
+widths leave the order among tied candidates to noise, which on scheduling
+models (tasks numbered in precedence order) loses first-fail's habit of
+placing tasks in that order.  The target of a node is the softmax of the
+expert's scores over its candidates, and the policy learns to rank
+candidates like the expert without running the probe.
 Features come from pccp_policy_features, i.e. exactly the values the search
 kernels feed the network.
 
@@ -25,7 +29,8 @@ from . import Model, Policy, propagate, policy_features, rcpsp
 from . import PCCP_FIXPOINT
 
 PROBE_TEMPERATURE = 0.05
-WIDTH_WEIGHT = 0.5  # expert score -= WIDTH_WEIGHT * log2(1 + domain width)
+WIDTH_WEIGHT = 1.5  # expert score -= WIDTH_WEIGHT * log2(1 + domain width)
+INDEX_WEIGHT = 2.0  # expert score -= INDEX_WEIGHT * branch index / branch count
 
 
 def _device():
@@ -33,9 +38,12 @@ def _device():
     return torch.device("cuda", torch.cuda.current_device())
 
 
-def collect(instances, nodes_per_model=256, seed=0, max_decisions=15):
+def collect(instances, nodes_per_model=256, seed=0, max_decisions=15, width_weight=WIDTH_WEIGHT,
+            index_weight=INDEX_WEIGHT):
     """Training groups from a list of scheduling instances.  Returns a dict of
-    CUDA tensors: features [R, 12], group_off [G + 1], target [R]."""
+    CUDA tensors: features [R, 12], group_off [G + 1], target [R].
+    width_weight: weight of first-fail's log2(1 + width) in the expert;
+    index_weight: weight of its tie-break (lower branch index first)."""
     import torch
     from synthetic import draw_partial_assignments
     dev = _device()
@@ -81,7 +89,8 @@ def collect(instances, nodes_per_model=256, seed=0, max_decisions=15):
         red = ((w_before.repeat(2) - w_after) / w_before.repeat(2)) * (1 - failed)
         width = (bub[node_idx, cand] - blb[node_idx, cand]).float()
         score = (failed[:c] + failed[c:]) * 2.0 + red[:c] + red[c:] \
-            - WIDTH_WEIGHT * torch.log2(1.0 + width)
+            - width_weight * torch.log2(1.0 + width) \
+            - index_weight * cand.float() / float(branch.numel())
         # groups: one per node, candidates in row-major order of (node, branch index)
         counts = torch.bincount(node_idx, minlength=lb.shape[0])
         target = torch.empty_like(score)
