@@ -657,10 +657,16 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
       const LinRow& row = short_rows[r];
       const size_t lane = r - t0;
       for (size_t k = 0; k < row.terms.size(); ++k) TERMS[tile + 32 * k + lane] = row.terms[k];
-      bool pos = true;  // flag 1: every coefficient positive
-      for (uint32_t t : row.terms) pos = pos && (static_cast<int32_t>(t) >> 16) > 0;
+      // flags: 1 every coefficient positive; 2 also every variable 0/1 at the root
+      bool pos = true, zero_one = true;
+      for (uint32_t t : row.terms) {
+        const int32_t v = static_cast<int32_t>(t & 0xffffu);
+        pos = pos && (static_cast<int32_t>(t) >> 16) > 0;
+        zero_one = zero_one && d->lb0[v] >= 0 && d->ub0[v] <= 1;
+      }
       L.push_back(make_int4(row.c, static_cast<int32_t>(tile + lane),
-                            static_cast<int32_t>(row.terms.size()), pos ? 1 : 0));
+                            static_cast<int32_t>(row.terms.size()),
+                            pos ? (zero_one ? 3 : 1) : 0));
     }
   }
   tile_start.push_back(TERMS.size());

@@ -58,7 +58,8 @@ static_assert(sizeof(StreamSeg) == 32, "segment record must be 32 bytes");
 // Row encodings (structure of arrays, one array per row kind):
 //   temporal  uint2 {x | y << 16, d}              x + d <= y
 //   reified   uint2 {x | y << 16, b | d << 16}    b <=> (x <= y && y < x + d), d int16
-//   linear    int4  {c, base, len, flags}         sum coef*var <= c; flags: 1 all coef > 0
+//   linear    int4  {c, base, len, flags}         sum coef*var <= c; flags: 1 all coef > 0,
+//                                                 2 and all vars 0/1 at the root
 //   term      uint32 var | coef << 16             coef int16
 // Linear rows of at most kShortRow terms are evaluated by one thread each and
 // stored in tiles of 32 rows, transposed: term t of the row in lane l of a
@@ -582,6 +583,21 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
     return;
   }
   if (S + span <= c) return;
+  if (h.w & 2) {
+    // positive coefficients over 0/1 variables: with slack0 = c - S, term k
+    // moves iff a * (ub - lb) > slack0, i.e. iff it is [0, 1] and a > slack0,
+    // and then to floor(slack0 / a) = 0.  The coefficient test comes first,
+    // so terms that cannot move skip their interval load.
+    const int slack0 = c - S;
+    for (int k = 0; k < len; ++k) {
+      const uint32_t t = tp[32 * k];
+      if ((static_cast<int>(t) >> 16) <= slack0) continue;
+      const int v = t & 0xffff;
+      const int2 D = ld_dom(st, v);
+      if (D.x == 0 && D.y == 1) tell_ub<kTrack>(w, v, 0, D.x, D.y, f);
+    }
+    return;
+  }
   for (int k = 0; k < len; ++k) {
     const uint32_t t = tp[32 * k];
     const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
