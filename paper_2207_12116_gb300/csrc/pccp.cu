@@ -671,8 +671,15 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   }
   tile_start.push_back(TERMS.size());
   for (const LinRow& row : long_rows) {
+    bool pos = true, zero_one = true;  // flags as for short rows
+    for (uint32_t t : row.terms) {
+      const int32_t v = static_cast<int32_t>(t & 0xffffu);
+      pos = pos && (static_cast<int32_t>(t) >> 16) > 0;
+      zero_one = zero_one && d->lb0[v] >= 0 && d->ub0[v] <= 1;
+    }
     LL.push_back(make_int4(row.c, static_cast<int32_t>(TERMS_LONG.size()),
-                           static_cast<int32_t>(row.terms.size()), 0));
+                           static_cast<int32_t>(row.terms.size()),
+                           pos ? (zero_one ? 3 : 1) : 0));
     TERMS_LONG.insert(TERMS_LONG.end(), row.terms.begin(), row.terms.end());
   }
   // variable -> linear rows holding it (short rows 0.., long rows |L|..),

@@ -493,12 +493,13 @@ __device__ __forceinline__ void eval_linear_warp_at(const Sweep& w, int4 h,
   int S = 0, span = 0;
   int v0 = 0, a0 = 0;
   int2 D0 = make_int2(0, 0);
+  const bool pos = h.w & 1;  // every coefficient positive: no sign selects
   for (int k = lane; k < len; k += 32) {
     const uint32_t t = tp[k];
     const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
     const int2 D = ld_dom(st, v);
-    const int mt = a > 0 ? a * D.x : a * D.y;
-    const int sp = a > 0 ? a * (D.y - D.x) : a * (D.x - D.y);
+    const int mt = (pos || a > 0) ? a * D.x : a * D.y;
+    const int sp = (pos || a > 0) ? a * (D.y - D.x) : a * (D.x - D.y);
     S += mt;
     span = max(span, sp);
     if (k < 32) {
@@ -514,6 +515,25 @@ __device__ __forceinline__ void eval_linear_warp_at(const Sweep& w, int4 h,
     return;
   }
   if (S + span <= c) return;
+  if (h.w & 2) {  // 0/1 variables: as in eval_linear_thread_at
+    const int slack0 = c - S;
+    for (int k = lane; k < len; k += 32) {
+      int v;
+      int2 D;
+      if (k < 32) {
+        if (a0 <= slack0) continue;
+        v = v0;
+        D = D0;
+      } else {
+        const uint32_t t = tp[k];
+        if ((static_cast<int>(t) >> 16) <= slack0) continue;
+        v = t & 0xffff;
+        D = ld_dom(st, v);
+      }
+      if (D.x == 0 && D.y == 1) tell_ub<kTrack>(w, v, 0, D.x, D.y, f);
+    }
+    return;
+  }
   for (int k = lane; k < len; k += 32) {
     int v, a;
     int2 D;
