@@ -29,7 +29,7 @@ struct PropArgs {
   int max_iter;
   int track_words;
   int table_global;   // 1: rows are read from the device image (too big for shared memory)
-  int stream_stages;  // table_global: buffers of each team's stream (kStream kernels)
+  int stream_stages;  // table_global: buffers of each team's stream (0: rows read in place)
   int reordered;      // 1: st uses the library's variable order (internal_of after the root)
 };
 
@@ -42,14 +42,15 @@ struct PropCtrl {
 
 // Instantiated for 1024-thread CTAs (one per SM) and for CTAs of up to 512
 // threads with three resident per SM (registers capped for 48 warps/SM);
-// kStream: the table is streamed (1024-thread variant only).
-template <int kMaxThreads, int kMinBlocks, bool kTrack, bool kStream>
+// kGlobal: the table is read from global memory (1024-thread variant only),
+// in place or, with stream_stages > 0, streamed.
+template <int kMaxThreads, int kMinBlocks, bool kTrack, bool kGlobal>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  // shared memory: [table image | kStream: one stream region per team | none]
+  // shared memory: [table image | kGlobal: one stream region per team, or none]
   //                [mbarrier 16 B][PropCtrl x teams][change words x teams][stores]
   const size_t stream_region = stream_bytes(a.stream_stages);
-  const size_t img_bytes = kStream ? stream_region * a.teams : (a.table_global ? 0 : a.image_bytes);
+  const size_t img_bytes = kGlobal ? stream_region * a.teams : a.image_bytes;
   uint8_t* img = smem;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + img_bytes);
   PropCtrl* ctrl_base = reinterpret_cast<PropCtrl*>(smem + img_bytes + 16);
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   int2* st_base = reinterpret_cast<int2*>(track_base + static_cast<size_t>(tw16) * a.teams);
 
   bool ok = true;
-  if (!a.table_global) {
+  if (!kGlobal) {
     if (threadIdx.x == 0) mbar_init(mbar, 1);
     ok = load_image(img, a.image, a.image_bytes, mbar, 0);
   }
@@ -74,14 +75,15 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   tm.nwarps = a.team_size >> 5;
   PropCtrl* ctrl = ctrl_base + team_id;
   int2* st = st_base + static_cast<size_t>(team_id) * a.n_vars;
-  const Tab tb = make_tab(a.table_global ? a.image : img);
+  const Tab tb = make_tab(kGlobal ? a.image : img);
   const Track tk = make_track(track_base + static_cast<size_t>(tw16) * team_id, tb.n_vars,
                               tb.n_lin + tb.n_lin_long);
   const int nv = a.n_vars;
   // the library's index of each of the caller's variables (after the root)
   const int32_t* internal_of = reinterpret_cast<const int32_t*>(a.root + nv);
   Streamer stream;
-  if (kStream)  // published by the barrier at the top of the store loop
+  const bool streamed = kGlobal && a.stream_stages > 0;
+  if (streamed)  // published by the barrier at the top of the store loop
     stream = stream_open(smem + stream_region * team_id, a.stream_stages, tb, a.image, tm, 0u);
 
   for (;;) {
@@ -120,8 +122,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
     const bool any_empty = team_bar_or(tm.bar, tm.nthr, empty);
     int status = kFailed, it = 0;
     if (!any_empty)
-      status = team_fixpoint<kTrack, kStream>(tb, st, tm, &ctrl->fc, tk, true, a.max_iter, it,
-                                              &stream);
+      status = team_fixpoint<kTrack, kGlobal>(tb, st, tm, &ctrl->fc, tk, true, a.max_iter, it,
+                                              streamed ? &stream : nullptr);
     for (int x = tm.tid; x < nv; x += tm.nthr) {
       const int2 D = st[a.reordered ? __ldg(internal_of + x) : x];
       lbs[x] = D.x;
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   }
   // every thread passed the barrier after its last segment: the copies in
   // flight are the prefetched ones
-  if (kStream) stream_close(stream);
+  if (streamed) stream_close(stream);
 }
 
 }  // namespace pccp

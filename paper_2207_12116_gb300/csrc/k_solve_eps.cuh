@@ -55,7 +55,7 @@ struct EpsArgs {
   int obj_ub;
   int track_words;
   int table_global;  // 1: rows are read from the device image
-  int stream_stages; // table_global: buffers of each team's stream (kStream kernels)
+  int stream_stages; // table_global: buffers of each team's stream (0: rows read in place)
   int x_words;       // learned strategy: feature rows per team (words)
   const PolicyDev* policy;
   int64_t node_limit;
@@ -95,7 +95,7 @@ __device__ __forceinline__ uint64_t eps_now_ns() {
 // the selection key (branch index in the low 32 bits).  Team-uniform result.
 // Broadcast slots follow the protocol of team_dfs: written before a barrier,
 // read after it, not rewritten before another barrier has passed.
-template <bool kTrack, bool kLearned, bool kStream>
+template <bool kTrack, bool kLearned, bool kGlobal>
 __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm, EpsCtrl* sc,
                                         const Track& tk, bool seeded, unsigned par,
                                         const EpsArgs& a, int& it, unsigned long long& key,
@@ -132,7 +132,7 @@ __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm,
   team_bar(tm.bar, tm.nthr);
   if (sc->stop) return kNodeStop;
   const int fst =
-      team_fixpoint<kTrack, kStream>(tb, st, tm, &sc->fc, tk, !seeded, a.max_iter, it, stream);
+      team_fixpoint<kTrack, kGlobal>(tb, st, tm, &sc->fc, tk, !seeded, a.max_iter, it, stream);
   if (fst == kError) return kNodeError;
   if (fst == kFailed) return kNodeFailed;
   unsigned long long* sel = &sc->sel[par];
@@ -267,12 +267,12 @@ __device__ __forceinline__ Team eps_team(const EpsArgs& a, int team_id) {
 // One breadth-first level: every input path is propagated once; failures
 // and solutions are counted; every other node pushes its two children
 // (left ub <= m, right lb >= m + 1) to the output level.
-template <bool kTrack, bool kLearned, bool kStream>
+template <bool kTrack, bool kLearned, bool kGlobal>
 __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
   const EpsSmem sm = eps_smem(smem, a, team_id);
-  if (!a.table_global) {
+  if (!kGlobal) {
     if (threadIdx.x == 0) mbar_init(sm.mbar, 1);
     if (!load_image(sm.img, a.image, a.image_bytes, sm.mbar, 0)) {
       if (threadIdx.x == 0) atomicExch(&a.g->error, 3);
@@ -282,11 +282,12 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && a.g->t0 == 0)
     atomicCAS(&a.g->t0, 0ull, static_cast<unsigned long long>(eps_now_ns()));
   const Team tm = eps_team(a, team_id);
-  const Tab tb = make_tab(a.table_global ? a.image : sm.img);
+  const Tab tb = make_tab(kGlobal ? a.image : sm.img);
   const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
   Streamer stream;
-  if (kStream)  // published by the barrier at the top of the work loop
+  const bool streamed = kGlobal && a.stream_stages > 0;
+  if (streamed)  // published by the barrier at the top of the work loop
     stream = stream_open(sm.stream, a.stream_stages, tb, a.image, tm, 0u);
   EpsCtrl* sc = sm.sc;
   unsigned long long nodes = 0, published = 0, fails = 0, sols = 0, iters = 0, evals = 0;
@@ -301,8 +302,9 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
     eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, tk, path, a.in_len);
     int it = 0;
     unsigned long long key = 0;
-    const int r = eps_node<kTrack, kLearned, kStream>(tb, sm.st, tm, sc, tk, false, par, a, it, key,
-                                                        a.in_len, sm.X, &stream);
+    const int r = eps_node<kTrack, kLearned, kGlobal>(tb, sm.st, tm, sc, tk, false, par, a, it, key,
+                                                        a.in_len, sm.X,
+                                                        streamed ? &stream : nullptr);
     par ^= 1u;
     if (r == kNodeStop) break;
     if (tm.tid == 0) {
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
     }
   }
   // every exit follows a team barrier after the team's last segment
-  if (kStream) stream_close(stream);
+  if (streamed) stream_close(stream);
   if (tm.tid == 0) {
     atomicAdd(&a.g->nodes, nodes);
     atomicAdd(&a.g->fails, fails);
@@ -363,12 +365,12 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
 }
 
 // Persistent teams search the subtrees under the frontier paths depth first.
-template <bool kTrack, bool kLearned, bool kStream>
+template <bool kTrack, bool kLearned, bool kGlobal>
 __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
   const EpsSmem sm = eps_smem(smem, a, team_id);
-  if (!a.table_global) {
+  if (!kGlobal) {
     if (threadIdx.x == 0) mbar_init(sm.mbar, 1);
     if (!load_image(sm.img, a.image, a.image_bytes, sm.mbar, 0)) {
       if (threadIdx.x == 0) atomicExch(&a.g->error, 3);
@@ -378,11 +380,12 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && a.g->t0 == 0)
     atomicCAS(&a.g->t0, 0ull, static_cast<unsigned long long>(eps_now_ns()));
   const Team tm = eps_team(a, team_id);
-  const Tab tb = make_tab(a.table_global ? a.image : sm.img);
+  const Tab tb = make_tab(kGlobal ? a.image : sm.img);
   const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
   Streamer stream;
-  if (kStream)  // published by the barrier at the top of the work loop
+  const bool streamed = kGlobal && a.stream_stages > 0;
+  if (streamed)  // published by the barrier at the top of the work loop
     stream = stream_open(sm.stream, a.stream_stages, tb, a.image, tm, 0u);
   EpsCtrl* sc = sm.sc;
   int2* stack = a.stacks + static_cast<size_t>(team_gid) * a.max_depth;
@@ -404,8 +407,9 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
     for (;;) {
       int it = 0;
       unsigned long long key = 0;
-      const int r = eps_node<kTrack, kLearned, kStream>(tb, sm.st, tm, sc, tk, seeded, par, a, it,
-                                                          key, depth, sm.X, &stream);
+      const int r = eps_node<kTrack, kLearned, kGlobal>(tb, sm.st, tm, sc, tk, seeded, par, a, it,
+                                                          key, depth, sm.X,
+                                                          streamed ? &stream : nullptr);
       par ^= 1u;
       if (r == kNodeStop) {
         done = true;
@@ -472,7 +476,7 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
     }
   }
   // every exit follows a team barrier after the team's last segment
-  if (kStream) stream_close(stream);
+  if (streamed) stream_close(stream);
   if (tm.tid == 0) {
     atomicAdd(&a.g->nodes, nodes);
     atomicAdd(&a.g->fails, fails);

@@ -83,7 +83,7 @@ struct SolveArgs {
   uint32_t max_image_bytes;  // 0 when the tables are read from global memory
   int max_track_words;
   int table_global;
-  int stream_stages;          // table_global: buffers of the stream (kStream kernels)
+  int stream_stages;          // table_global: buffers of the stream (0: rows read in place)
   int x_words;                // learned strategy: feature rows per team (words)
   int max_vars_smem;          // store slots reserved per CTA
   const PolicyDev* policy;
@@ -113,7 +113,7 @@ constexpr uint32_t kRightBit = 0x80000000u;
 // All control decisions are made by thread 0 and broadcast through shared
 // memory; every broadcast slot is written before a barrier and read after it,
 // and never rewritten before the next barrier that follows all its reads.
-template <bool kTrack, bool kLearned, bool kStream>
+template <bool kTrack, bool kLearned, bool kGlobal>
 __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st, const Team& tm,
                          SearchCtrl* sc, const Track& tk, int2* stack, const SolveArgs& a,
                          int max_iter, int32_t* witness, InstanceResult* out, uint32_t* X,
@@ -159,7 +159,7 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
     if (sc->stop) break;
     int it = 0;
     const int fst =
-        team_fixpoint<kTrack, kStream>(tb, st, tm, &sc->fc, tk, !seeded, max_iter, it, stream);
+        team_fixpoint<kTrack, kGlobal>(tb, st, tm, &sc->fc, tk, !seeded, max_iter, it, stream);
     if (tm.tid == 0) {
       ++nodes;
       iters += it;
@@ -283,12 +283,13 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
   }
 }
 
-template <bool kTrack, bool kLearned, bool kStream>
+template <bool kTrack, bool kLearned, bool kGlobal>
 __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  // [table image | kStream: the stream region | none][mbarrier][SearchCtrl]
+  // [table image | kGlobal: the stream region, or none][mbarrier][SearchCtrl]
   // [change words][store][feature rows]
-  const size_t head = kStream ? stream_bytes(a.stream_stages) : a.max_image_bytes;
+  const size_t head = kGlobal ? stream_bytes(a.stream_stages) : a.max_image_bytes;
+  const bool streamed = kGlobal && a.stream_stages > 0;
   uint8_t* img = smem;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + head);
   SearchCtrl* sc = reinterpret_cast<SearchCtrl*>(smem + head + 16);
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
     const int i = sc->next;
     if (i >= a.n_inst) break;
     const InstanceDesc d = a.inst[i];
-    if (!a.table_global) {
+    if (!kGlobal) {
       if (!load_image(img, d.image, d.image_bytes, mbar, parity)) {
         if (threadIdx.x == 0) {
           a.res[i].status = PCCP_RES_LIMIT;
@@ -328,18 +329,19 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
     } else {
       __syncthreads();
     }
-    const Tab tb = make_tab(a.table_global ? d.image : img);
+    const Tab tb = make_tab(kGlobal ? d.image : img);
     const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
-    if (kStream) {  // the previous model's prefetched copies land first
+    if (streamed) {  // the previous model's prefetched copies land first
       if (open) seq = stream_close(stream);
       stream = stream_open(img, a.stream_stages, tb, d.image, tm, seq);
       open = true;
       __syncthreads();
     }
-    team_dfs<kTrack, kLearned, kStream>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
-                                        a.witness + d.witness_off, &a.res[i], X, &stream);
+    team_dfs<kTrack, kLearned, kGlobal>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
+                                        a.witness + d.witness_off, &a.res[i], X,
+                                        streamed ? &stream : nullptr);
   }
-  if (kStream && open) stream_close(stream);
+  if (streamed && open) stream_close(stream);
 }
 
 // -------------------------------------------------------------- host model
@@ -893,11 +895,11 @@ int policy_x_words(const pccp_solve_opts* o, int max_branch) {
   return o->strategy == PCCP_LEARNED ? 8 * ((max_branch + 15) & ~15) : 0;
 }
 
-// The k_solve instantiation for a search's options (stream: the tables are
-// streamed).
+// The k_solve instantiation for a search's options (global: the tables are
+// read from global memory, in place or streamed).
 using SolveKernel = void (*)(SolveArgs);
-SolveKernel solve_kernel(const pccp_solve_opts* o, bool stream) {
-  if (stream) {
+SolveKernel solve_kernel(const pccp_solve_opts* o, bool global) {
+  if (global) {
     if (o->strategy == PCCP_LEARNED) return k_solve<false, true, true>;
     return o->skip_stable ? k_solve<true, false, true> : k_solve<false, false, true>;
   }
@@ -988,7 +990,7 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   const size_t smem = base + static_cast<size_t>(teams) * (per_team + stream_bytes(stages));
   const bool track = cfg && cfg->skip_stable;
   const auto kern =
-      stages > 0 ? (track ? k_propagate<1024, 1, true, true> : k_propagate<1024, 1, false, true>)
+      global ? (track ? k_propagate<1024, 1, true, true> : k_propagate<1024, 1, false, true>)
       : (teams * team <= 512)
           ? (track ? k_propagate<512, 3, true, false> : k_propagate<512, 3, false, false>)
           : (track ? k_propagate<1024, 1, true, false> : k_propagate<1024, 1, false, false>);
@@ -1260,7 +1262,7 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
                                       opts->stream_table, max_seg, &stages);
   if (smem > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   if (global && opts->threads <= 0) threads = 1024;
-  const auto ksolve = solve_kernel(opts, stages > 0);
+  const auto ksolve = solve_kernel(opts, global);
   PCCP_CUDA(cudaFuncSetAttribute(ksolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
   int per_sm = 0;
@@ -1397,7 +1399,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   const bool learned = o->strategy == PCCP_LEARNED;
   using EpsKernel = void (*)(EpsArgs);
   EpsKernel kexp, ksol;
-  if (stages > 0) {
+  if (global) {
     kexp = learned ? k_eps_expand<false, true, true>
                    : (o->skip_stable ? k_eps_expand<true, false, true> : k_eps_expand<false, false, true>);
     ksol = learned ? k_eps_solve<false, true, true>

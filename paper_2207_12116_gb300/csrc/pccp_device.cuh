@@ -402,9 +402,25 @@ __device__ __forceinline__ void reified_rule(int2 X, int2 Y, int2 B, int d, int&
   if (entNA || entNB) nub = min(nub, 0);  // not (A and B) entailed: not b
 }
 
+// True when a reified rule b <=> (x <= y and y <= x + d - 1) can tell
+// nothing on a snapshot with non-empty intervals, given g1 = lb y - ub x and
+// g2 = lb x - ub y: b unfixed with neither the conjunction (g1 >= 0,
+// g2 >= 1 - d) nor its negation (g2 >= 1 or g1 >= d) entailed; or b = 1 with
+// the conjunction entailed; or b = 0 with the negation entailed (every tell
+// of the rule is then already implied by the bounds).  Anything else,
+// including an empty b, goes through the full rule.
+__device__ __forceinline__ bool rule_quiet(int2 B, int g1, int g2, int d) {
+  const bool t = g1 >= 0 && g2 >= 1 - d;
+  const bool n = g2 >= 1 || g1 >= d;
+  return (B.x == 0 && B.y == 1) ? !(t || n) : (B.x == B.y && (B.x == 1 ? t : n));
+}
+
 // Reified row, evaluated on one snapshot; the tells (rare once the store
-// settles) sit behind one branch.
-template <bool kTrack>
+// settles) sit behind one branch.  kQuiet: rows that cannot tell anything
+// (rule_quiet) leave before the rule; that pays where loads are slow (tables
+// read from global memory) and costs where issue is the limit (tables in
+// shared memory), so the kernels for global tables use it.
+template <bool kTrack, bool kQuiet>
 __device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f) {
   const int x = row.x & 0xffff, y = row.x >> 16;
   const int b = row.y & 0xffff, d = static_cast<int>(row.y) >> 16;
@@ -416,6 +432,7 @@ __device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f
   f.evals += 1;
   f.bytes += 40;
   const int2 X = ld_dom(w.st, x), Y = ld_dom(w.st, y), B = ld_dom(w.st, b);
+  if (kQuiet && X.x <= X.y && Y.x <= Y.y && rule_quiet(B, Y.x - X.y, X.x - Y.y, d)) return;
   int nlx = X.x, nux = X.y, nly = Y.x, nuy = Y.y, nlb = B.x, nub = B.y;
   reified_rule(X, Y, B, d, nlx, nux, nly, nuy, nlb, nub);
   if (nlx > X.x || nux < X.y || nly > Y.x || nuy < Y.y || nlb > B.x || nub < B.y) {
@@ -432,7 +449,7 @@ __device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f
 // b1 <=> (x <= y and y < x + d1) and b2 <=> (y <= x and x < y + d2) (the
 // overlap Booleans b_{i,j} and b_{j,i} of the scheduling model): both rules on
 // one snapshot, so x and y are loaded once for two rows.
-template <bool kTrack>
+template <bool kTrack, bool kQuiet>
 __device__ __forceinline__ void eval_reified_pair(const Sweep& w, uint4 row, Flags& f) {
   const int x = row.x & 0xffff, y = row.x >> 16;
   const int b1 = row.y & 0xffff, d1 = static_cast<int>(row.y) >> 16;
@@ -447,6 +464,11 @@ __device__ __forceinline__ void eval_reified_pair(const Sweep& w, uint4 row, Fla
   f.bytes += 80;
   const int2 X = ld_dom(w.st, x), Y = ld_dom(w.st, y);
   const int2 B1 = ld_dom(w.st, b1), B2 = ld_dom(w.st, b2);
+  if (kQuiet) {  // neither rule can tell anything (rule 2 swaps x and y)
+    const int g1 = Y.x - X.y, g2 = X.x - Y.y;
+    if (X.x <= X.y && Y.x <= Y.y && rule_quiet(B1, g1, g2, d1) && rule_quiet(B2, g2, g1, d2))
+      return;
+  }
   int nlx = X.x, nux = X.y, nly = Y.x, nuy = Y.y;
   int nlb1 = B1.x, nub1 = B1.y, nlb2 = B2.x, nub2 = B2.y;
   reified_rule(X, Y, B1, d1, nlx, nux, nly, nuy, nlb1, nub1);
@@ -636,11 +658,12 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
 // eventless loop).  Rows of one kind run back to back so warps stay uniform:
 // a thread per reified, temporal and short linear row, a warp per long
 // linear row.
-template <bool kTrack>
+template <bool kTrack, bool kQuiet>
 __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags& f) {
   const Tab& tb = w.tb;
-  for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr) eval_reified_pair<kTrack>(w, tb.rfp[r], f);
-  for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack>(w, tb.rf[r], f);
+  for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr)
+    eval_reified_pair<kTrack, kQuiet>(w, tb.rfp[r], f);
+  for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack, kQuiet>(w, tb.rf[r], f);
   for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
   for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) {
     if (skip_linear_short<kTrack>(w, r, f)) continue;
@@ -790,12 +813,13 @@ __device__ __forceinline__ void sweep_rows_streamed(const Sweep& w, const Team& 
       switch (s.kind) {
         case kSegPairs: {
           const uint4* R = reinterpret_cast<const uint4*>(B);
-          for (int i = tm.tid; i < s.count; i += tm.nthr) eval_reified_pair<kTrack>(w, R[i], f);
+          for (int i = tm.tid; i < s.count; i += tm.nthr)
+            eval_reified_pair<kTrack, true>(w, R[i], f);
           break;
         }
         case kSegSingles: {
           const uint2* R = reinterpret_cast<const uint2*>(B);
-          for (int i = tm.tid; i < s.count; i += tm.nthr) eval_reified<kTrack>(w, R[i], f);
+          for (int i = tm.tid; i < s.count; i += tm.nthr) eval_reified<kTrack, true>(w, R[i], f);
           break;
         }
         case kSegTemporal: {
@@ -877,10 +901,10 @@ __device__ __forceinline__ void count_sweeps(const Tab& tb, const Team& tm, FixC
 // or the change buffers before the next team barrier after this returns.
 // Team-uniform return value; fc->evals / fc->bytes are valid after return
 // for the team's thread 0 (for every thread after the next team barrier).
-// kStream: the table is read from global memory in segments through the
-// team's stream *sm (otherwise rows are read where tb points).  A stream that
-// lost a copy ends the loop with kError.
-template <bool kTrack, bool kStream = false>
+// kGlobal: the table is in global memory; with a stream (sm not null) its
+// rows come in segments through the team's stream, else they are read where
+// tb points.  A stream that lost a copy ends the loop with kError.
+template <bool kTrack, bool kGlobal = false>
 __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team& tm, FixCtrl* fc,
                                              const Track& tk, bool full, int max_iter,
                                              int& iters, Streamer* sm = nullptr) {
@@ -893,10 +917,10 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
     }
     const Sweep w{tb, st, tk, cur, tk.chg + prv * tk.W, tk.dl + prv * tk.WL, full || !kTrack};
     Flags f{false, false, 0, 0};
-    if (kStream)
+    if (kGlobal && sm)
       sweep_rows_streamed<kTrack>(w, tm, f, *sm);
     else
-      sweep_rows<kTrack>(w, tm, f);
+      sweep_rows<kTrack, kGlobal>(w, tm, f);
     if (kTrack) {  // rows skipped vary: count what ran
       const int ev = __reduce_add_sync(0xffffffffu, f.evals);
       const int by = __reduce_add_sync(0xffffffffu, f.bytes);
@@ -909,7 +933,7 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
     ++it;
     full = false;
     const bool any = team_bar_or(tm.bar, tm.nthr, f.ch || f.fl);
-    if (kStream && ld_relaxed(&sm->ctl->err)) {
+    if (kGlobal && sm && ld_relaxed(&sm->ctl->err)) {
       iters = it;
       count_sweeps<kTrack>(tb, tm, fc, it);
       return kError;
