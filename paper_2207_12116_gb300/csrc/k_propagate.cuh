@@ -43,8 +43,8 @@ struct PropCtrl {
 // Instantiated for 1024-thread CTAs (one per SM) and for CTAs of up to 512
 // threads with three resident per SM (registers capped for 48 warps/SM);
 // kGlobal: the table is read from global memory (1024-thread variant only),
-// in place or, with stream_stages > 0, streamed.
-template <int kMaxThreads, int kMinBlocks, bool kTrack, bool kGlobal>
+// in place or, with kStream (stream_stages > 0), streamed.
+template <int kMaxThreads, int kMinBlocks, bool kTrack, bool kGlobal, bool kStream>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   // shared memory: [table image | kGlobal: one stream region per team, or none]
@@ -82,8 +82,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   // the library's index of each of the caller's variables (after the root)
   const int32_t* internal_of = reinterpret_cast<const int32_t*>(a.root + nv);
   Streamer stream;
-  const bool streamed = kGlobal && a.stream_stages > 0;
-  if (streamed)  // published by the barrier at the top of the store loop
+  if (kStream)  // published by the barrier at the top of the store loop
     stream = stream_open(smem + stream_region * team_id, a.stream_stages, tb, a.image, tm, 0u);
 
   for (;;) {
@@ -122,8 +121,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
     const bool any_empty = team_bar_or(tm.bar, tm.nthr, empty);
     int status = kFailed, it = 0;
     if (!any_empty)
-      status = team_fixpoint<kTrack, kGlobal>(tb, st, tm, &ctrl->fc, tk, true, a.max_iter, it,
-                                              streamed ? &stream : nullptr);
+      status = team_fixpoint<kTrack, kGlobal, kStream>(tb, st, tm, &ctrl->fc, tk, true,
+                                                       a.max_iter, it, &stream);
     for (int x = tm.tid; x < nv; x += tm.nthr) {
       const int2 D = st[a.reordered ? __ldg(internal_of + x) : x];
       lbs[x] = D.x;
@@ -140,7 +139,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   }
   // every thread passed the barrier after its last segment: the copies in
   // flight are the prefetched ones
-  if (streamed) stream_close(stream);
+  if (kStream) stream_close(stream);
 }
 
 }  // namespace pccp

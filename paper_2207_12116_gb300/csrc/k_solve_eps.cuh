@@ -95,7 +95,7 @@ __device__ __forceinline__ uint64_t eps_now_ns() {
 // the selection key (branch index in the low 32 bits).  Team-uniform result.
 // Broadcast slots follow the protocol of team_dfs: written before a barrier,
 // read after it, not rewritten before another barrier has passed.
-template <bool kTrack, bool kLearned, bool kGlobal>
+template <bool kTrack, bool kLearned, bool kGlobal, bool kStream>
 __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm, EpsCtrl* sc,
                                         const Track& tk, bool seeded, unsigned par,
                                         const EpsArgs& a, int& it, unsigned long long& key,
@@ -132,7 +132,8 @@ __device__ __forceinline__ int eps_node(const Tab& tb, int2* st, const Team& tm,
   team_bar(tm.bar, tm.nthr);
   if (sc->stop) return kNodeStop;
   const int fst =
-      team_fixpoint<kTrack, kGlobal>(tb, st, tm, &sc->fc, tk, !seeded, a.max_iter, it, stream);
+      team_fixpoint<kTrack, kGlobal, kStream>(tb, st, tm, &sc->fc, tk, !seeded, a.max_iter, it,
+                                              stream);
   if (fst == kError) return kNodeError;
   if (fst == kFailed) return kNodeFailed;
   unsigned long long* sel = &sc->sel[par];
@@ -267,7 +268,7 @@ __device__ __forceinline__ Team eps_team(const EpsArgs& a, int team_id) {
 // One breadth-first level: every input path is propagated once; failures
 // and solutions are counted; every other node pushes its two children
 // (left ub <= m, right lb >= m + 1) to the output level.
-template <bool kTrack, bool kLearned, bool kGlobal>
+template <bool kTrack, bool kLearned, bool kGlobal, bool kStream>
 __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
@@ -286,8 +287,7 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
   const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
   Streamer stream;
-  const bool streamed = kGlobal && a.stream_stages > 0;
-  if (streamed)  // published by the barrier at the top of the work loop
+  if (kStream)  // published by the barrier at the top of the work loop
     stream = stream_open(sm.stream, a.stream_stages, tb, a.image, tm, 0u);
   EpsCtrl* sc = sm.sc;
   unsigned long long nodes = 0, published = 0, fails = 0, sols = 0, iters = 0, evals = 0;
@@ -302,9 +302,8 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
     eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, tk, path, a.in_len);
     int it = 0;
     unsigned long long key = 0;
-    const int r = eps_node<kTrack, kLearned, kGlobal>(tb, sm.st, tm, sc, tk, false, par, a, it, key,
-                                                        a.in_len, sm.X,
-                                                        streamed ? &stream : nullptr);
+    const int r = eps_node<kTrack, kLearned, kGlobal, kStream>(tb, sm.st, tm, sc, tk, false, par, a, it,
+                                                                 key, a.in_len, sm.X, &stream);
     par ^= 1u;
     if (r == kNodeStop) break;
     if (tm.tid == 0) {
@@ -353,7 +352,7 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
     }
   }
   // every exit follows a team barrier after the team's last segment
-  if (streamed) stream_close(stream);
+  if (kStream) stream_close(stream);
   if (tm.tid == 0) {
     atomicAdd(&a.g->nodes, nodes);
     atomicAdd(&a.g->fails, fails);
@@ -365,7 +364,7 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
 }
 
 // Persistent teams search the subtrees under the frontier paths depth first.
-template <bool kTrack, bool kLearned, bool kGlobal>
+template <bool kTrack, bool kLearned, bool kGlobal, bool kStream>
 __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int team_id = threadIdx.x / a.team_size;
@@ -384,8 +383,7 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
   const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
   Streamer stream;
-  const bool streamed = kGlobal && a.stream_stages > 0;
-  if (streamed)  // published by the barrier at the top of the work loop
+  if (kStream)  // published by the barrier at the top of the work loop
     stream = stream_open(sm.stream, a.stream_stages, tb, a.image, tm, 0u);
   EpsCtrl* sc = sm.sc;
   int2* stack = a.stacks + static_cast<size_t>(team_gid) * a.max_depth;
@@ -407,9 +405,8 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
     for (;;) {
       int it = 0;
       unsigned long long key = 0;
-      const int r = eps_node<kTrack, kLearned, kGlobal>(tb, sm.st, tm, sc, tk, seeded, par, a, it,
-                                                          key, depth, sm.X,
-                                                          streamed ? &stream : nullptr);
+      const int r = eps_node<kTrack, kLearned, kGlobal, kStream>(tb, sm.st, tm, sc, tk, seeded, par, a,
+                                                                   it, key, depth, sm.X, &stream);
       par ^= 1u;
       if (r == kNodeStop) {
         done = true;
@@ -476,7 +473,7 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
     }
   }
   // every exit follows a team barrier after the team's last segment
-  if (streamed) stream_close(stream);
+  if (kStream) stream_close(stream);
   if (tm.tid == 0) {
     atomicAdd(&a.g->nodes, nodes);
     atomicAdd(&a.g->fails, fails);

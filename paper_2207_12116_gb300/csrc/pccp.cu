@@ -113,7 +113,7 @@ constexpr uint32_t kRightBit = 0x80000000u;
 // All control decisions are made by thread 0 and broadcast through shared
 // memory; every broadcast slot is written before a barrier and read after it,
 // and never rewritten before the next barrier that follows all its reads.
-template <bool kTrack, bool kLearned, bool kGlobal>
+template <bool kTrack, bool kLearned, bool kGlobal, bool kStream>
 __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st, const Team& tm,
                          SearchCtrl* sc, const Track& tk, int2* stack, const SolveArgs& a,
                          int max_iter, int32_t* witness, InstanceResult* out, uint32_t* X,
@@ -159,7 +159,8 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
     if (sc->stop) break;
     int it = 0;
     const int fst =
-        team_fixpoint<kTrack, kGlobal>(tb, st, tm, &sc->fc, tk, !seeded, max_iter, it, stream);
+        team_fixpoint<kTrack, kGlobal, kStream>(tb, st, tm, &sc->fc, tk, !seeded, max_iter, it,
+                                                stream);
     if (tm.tid == 0) {
       ++nodes;
       iters += it;
@@ -283,13 +284,13 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
   }
 }
 
-template <bool kTrack, bool kLearned, bool kGlobal>
+template <bool kTrack, bool kLearned, bool kGlobal, bool kStream>
 __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   // [table image | kGlobal: the stream region, or none][mbarrier][SearchCtrl]
   // [change words][store][feature rows]
   const size_t head = kGlobal ? stream_bytes(a.stream_stages) : a.max_image_bytes;
-  const bool streamed = kGlobal && a.stream_stages > 0;
+
   uint8_t* img = smem;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + head);
   SearchCtrl* sc = reinterpret_cast<SearchCtrl*>(smem + head + 16);
@@ -331,17 +332,17 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
     }
     const Tab tb = make_tab(kGlobal ? d.image : img);
     const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
-    if (streamed) {  // the previous model's prefetched copies land first
+    if (kStream) {  // the previous model's prefetched copies land first
       if (open) seq = stream_close(stream);
       stream = stream_open(img, a.stream_stages, tb, d.image, tm, seq);
       open = true;
       __syncthreads();
     }
-    team_dfs<kTrack, kLearned, kGlobal>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
-                                        a.witness + d.witness_off, &a.res[i], X,
-                                        streamed ? &stream : nullptr);
+    team_dfs<kTrack, kLearned, kGlobal, kStream>(tb, d.root, st, tm, sc, tk, stack, a,
+                                                 d.max_iter, a.witness + d.witness_off,
+                                                 &a.res[i], X, &stream);
   }
-  if (streamed && open) stream_close(stream);
+  if (kStream && open) stream_close(stream);
 }
 
 // -------------------------------------------------------------- host model
@@ -896,15 +897,17 @@ int policy_x_words(const pccp_solve_opts* o, int max_branch) {
 }
 
 // The k_solve instantiation for a search's options (global: the tables are
-// read from global memory, in place or streamed).
+// read from global memory; stream: streamed through shared memory).
 using SolveKernel = void (*)(SolveArgs);
-SolveKernel solve_kernel(const pccp_solve_opts* o, bool global) {
-  if (global) {
-    if (o->strategy == PCCP_LEARNED) return k_solve<false, true, true>;
-    return o->skip_stable ? k_solve<true, false, true> : k_solve<false, false, true>;
-  }
-  if (o->strategy == PCCP_LEARNED) return k_solve<false, true, false>;
-  return o->skip_stable ? k_solve<true, false, false> : k_solve<false, false, false>;
+template <bool kGlobal, bool kStream>
+SolveKernel solve_kernel_t(const pccp_solve_opts* o) {
+  if (o->strategy == PCCP_LEARNED) return k_solve<false, true, kGlobal, kStream>;
+  return o->skip_stable ? k_solve<true, false, kGlobal, kStream>
+                        : k_solve<false, false, kGlobal, kStream>;
+}
+SolveKernel solve_kernel(const pccp_solve_opts* o, bool global, bool stream) {
+  if (stream) return solve_kernel_t<true, true>(o);
+  return global ? solve_kernel_t<true, false>(o) : solve_kernel_t<false, false>(o);
 }
 
 // Strategy and policy checks shared by the search entry points.
@@ -990,10 +993,15 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   const size_t smem = base + static_cast<size_t>(teams) * (per_team + stream_bytes(stages));
   const bool track = cfg && cfg->skip_stable;
   const auto kern =
-      global ? (track ? k_propagate<1024, 1, true, true> : k_propagate<1024, 1, false, true>)
+      stages > 0 ? (track ? k_propagate<1024, 1, true, true, true>
+                          : k_propagate<1024, 1, false, true, true>)
+      : global   ? (track ? k_propagate<1024, 1, true, true, false>
+                          : k_propagate<1024, 1, false, true, false>)
       : (teams * team <= 512)
-          ? (track ? k_propagate<512, 3, true, false> : k_propagate<512, 3, false, false>)
-          : (track ? k_propagate<1024, 1, true, false> : k_propagate<1024, 1, false, false>);
+          ? (track ? k_propagate<512, 3, true, false, false>
+                   : k_propagate<512, 3, false, false, false>)
+          : (track ? k_propagate<1024, 1, true, false, false>
+                   : k_propagate<1024, 1, false, false, false>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -1262,7 +1270,7 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
                                       opts->stream_table, max_seg, &stages);
   if (smem > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   if (global && opts->threads <= 0) threads = 1024;
-  const auto ksolve = solve_kernel(opts, global);
+  const auto ksolve = solve_kernel(opts, global, stages > 0);
   PCCP_CUDA(cudaFuncSetAttribute(ksolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
   int per_sm = 0;
@@ -1373,6 +1381,18 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
 
 namespace {
 
+// The EPS kernel pair for a search's options.
+template <bool kGlobal, bool kStream>
+void eps_kernels(bool learned, bool skip_stable, void (**kexp)(EpsArgs),
+                 void (**ksol)(EpsArgs)) {
+  *kexp = learned ? k_eps_expand<false, true, kGlobal, kStream>
+                  : (skip_stable ? k_eps_expand<true, false, kGlobal, kStream>
+                                 : k_eps_expand<false, false, kGlobal, kStream>);
+  *ksol = learned ? k_eps_solve<false, true, kGlobal, kStream>
+                  : (skip_stable ? k_eps_solve<true, false, kGlobal, kStream>
+                                 : k_eps_solve<false, false, kGlobal, kStream>);
+}
+
 // Parallel search of one model: breadth-first frontier growth, then one
 // persistent launch over the frontier's subproblems (k_solve_eps.cuh).
 int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* res,
@@ -1399,19 +1419,12 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   const bool learned = o->strategy == PCCP_LEARNED;
   using EpsKernel = void (*)(EpsArgs);
   EpsKernel kexp, ksol;
-  if (global) {
-    kexp = learned ? k_eps_expand<false, true, true>
-                   : (o->skip_stable ? k_eps_expand<true, false, true> : k_eps_expand<false, false, true>);
-    ksol = learned ? k_eps_solve<false, true, true>
-                   : (o->skip_stable ? k_eps_solve<true, false, true> : k_eps_solve<false, false, true>);
-  } else {
-    kexp = learned ? k_eps_expand<false, true, false>
-                   : (o->skip_stable ? k_eps_expand<true, false, false>
-                                     : k_eps_expand<false, false, false>);
-    ksol = learned ? k_eps_solve<false, true, false>
-                   : (o->skip_stable ? k_eps_solve<true, false, false>
-                                     : k_eps_solve<false, false, false>);
-  }
+  if (stages > 0)
+    eps_kernels<true, true>(learned, o->skip_stable, &kexp, &ksol);
+  else if (global)
+    eps_kernels<true, false>(learned, o->skip_stable, &kexp, &ksol);
+  else
+    eps_kernels<false, false>(learned, o->skip_stable, &kexp, &ksol);
   PCCP_CUDA(cudaFuncSetAttribute(kexp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
   PCCP_CUDA(cudaFuncSetAttribute(ksol, cudaFuncAttributeMaxDynamicSharedMemorySize,

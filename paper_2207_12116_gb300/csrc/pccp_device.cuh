@@ -901,10 +901,10 @@ __device__ __forceinline__ void count_sweeps(const Tab& tb, const Team& tm, FixC
 // or the change buffers before the next team barrier after this returns.
 // Team-uniform return value; fc->evals / fc->bytes are valid after return
 // for the team's thread 0 (for every thread after the next team barrier).
-// kGlobal: the table is in global memory; with a stream (sm not null) its
-// rows come in segments through the team's stream, else they are read where
+// kGlobal: the table is in global memory; kStream (with kGlobal): its rows
+// come in segments through the team's stream *sm, else they are read where
 // tb points.  A stream that lost a copy ends the loop with kError.
-template <bool kTrack, bool kGlobal = false>
+template <bool kTrack, bool kGlobal = false, bool kStream = false>
 __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team& tm, FixCtrl* fc,
                                              const Track& tk, bool full, int max_iter,
                                              int& iters, Streamer* sm = nullptr) {
@@ -917,7 +917,7 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
     }
     const Sweep w{tb, st, tk, cur, tk.chg + prv * tk.W, tk.dl + prv * tk.WL, full || !kTrack};
     Flags f{false, false, 0, 0};
-    if (kGlobal && sm)
+    if (kStream)
       sweep_rows_streamed<kTrack>(w, tm, f, *sm);
     else
       sweep_rows<kTrack, kGlobal>(w, tm, f);
@@ -933,7 +933,7 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
     ++it;
     full = false;
     const bool any = team_bar_or(tm.bar, tm.nthr, f.ch || f.fl);
-    if (kGlobal && sm && ld_relaxed(&sm->ctl->err)) {
+    if (kStream && ld_relaxed(&sm->ctl->err)) {
       iters = it;
       count_sweeps<kTrack>(tb, tm, fc, it);
       return kError;
