@@ -162,13 +162,32 @@ typedef struct {
 /* pccp_propagate with an explicit launch shape (cfg may be NULL) and an
  * optional work report: work is NULL or a DEVICE int32 [n_stores][2]
  * receiving, per store, the rows evaluated and the algorithmic bytes they
- * read (rows, operand bounds, change-tracking words).  Rows whose variables
- * did not change since their last evaluation are not evaluated again
- * (skipping stable propagators, Sec. 6); the fixed point is unchanged.
- * Returns PCCP_ERR_SMEM if the requested teams do not fit shared memory. */
+ * read (rows, operand bounds, change-tracking words).  With
+ * cfg->skip_stable, rows whose variables did not change since their last
+ * evaluation are not evaluated again (skipping stable propagators, Sec. 6);
+ * the fixed point is unchanged.  Returns PCCP_ERR_SMEM if the requested
+ * teams do not fit shared memory. */
 int pccp_propagate_ex(const pccp_model* model, int32_t n_stores, int32_t* lb, int32_t* ub,
                       int32_t* status, int32_t* iterations, int32_t* work,
                       const pccp_launch_config* cfg, void* stream);
+
+/* pccp_propagate for stores that live in HOST memory: lb, ub are HOST int32
+ * [n_stores][n_vars], updated in place with the fixed points; status and
+ * iterations (may be NULL) are HOST int32 [n_stores].  The stores travel in
+ * chunks of chunk_stores (<= 0: a default of about a quarter of the batch):
+ * while one chunk is propagated on `stream`, the next is copied in and the
+ * previous one copied out on two streams of the model's own, through two
+ * device slots.  Streams, events and slots are created on the model's first
+ * such call, grown for larger chunks and freed with the model; calls on one
+ * model are serialised (the host thread waits for the one in progress).
+ * Page-locked host memory (cudaHostAlloc, cudaHostRegister, a pinned torch
+ * tensor) lets the copies overlap; pageable memory works but serialises
+ * them.  The copies start after the work already queued on `stream`, and
+ * later work on `stream` follows them.  Synchronous: returns once every
+ * result is in host memory.  Errors: INVALID, SMEM, CUDA. */
+int pccp_propagate_host(const pccp_model* model, int32_t n_stores, int32_t* lb, int32_t* ub,
+                        int32_t* status, int32_t* iterations, int32_t chunk_stores,
+                        void* stream);
 
 /* ---- search ------------------------------------------------------------ */
 

@@ -29,7 +29,8 @@ __all__ = ["Model", "pccp_model_create", "pccp_model_destroy", "pccp_model_get_i
            "pccp_batch_results", "pccp_batch_destroy", "Batch", "Policy",
            "pccp_policy_create", "pccp_policy_destroy", "pccp_policy_get_weights",
            "pccp_policy_features", "pccp_policy_score", "pccp_policy_train_step",
-           "pccp_error_string", "propagate", "propagate_host", "solve", "solve_batch",
+           "pccp_error_string", "propagate", "propagate_host", "pccp_propagate_host", "solve",
+           "solve_batch",
            "PccpError", "load", "library_path", "pccp_probe", "roofline_probes"]
 
 
@@ -253,15 +254,37 @@ def propagate(model: Model, lb, ub, status=None, iterations=None, config=None, s
     return status, iterations
 
 
-def propagate_host(model: Model, lb, ub, device="cuda", config=None, stream=None):
-    """End-to-end form: host (pinned) int32 tensors in, host tensors out.
-    Copies the stores to the device, propagates, copies the results back."""
+def pccp_propagate_host(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr, chunk_stores,
+                        stream):
+    return load().pccp_propagate_host(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr,
+                                      chunk_stores, stream)
+
+
+def propagate_host(model: Model, lb, ub, status=None, iterations=None, chunk_stores=0,
+                   stream=None):
+    """End-to-end form (pccp_propagate_host): HOST int32 tensors [n, n_vars]
+    (pin them, e.g. torch.empty(..., pin_memory=True), for copies that
+    overlap the propagation), updated in place with the fixed points.
+    Returns (status, iterations), host int32 tensors [n]."""
     import torch
-    dlb = lb.to(device, non_blocking=True)
-    dub = ub.to(device, non_blocking=True)
-    st, it = propagate(model, dlb, dub, config=config, stream=stream)
-    out = (dlb.to("cpu", non_blocking=False), dub.to("cpu"), st.to("cpu"), it.to("cpu"))
-    return out
+    if lb.dtype != torch.int32 or ub.dtype != torch.int32 or lb.is_cuda or ub.is_cuda:
+        raise PccpError(PCCP_ERR_INVALID, "lb/ub must be int32 host tensors")
+    if not lb.is_contiguous() or not ub.is_contiguous() or lb.shape != ub.shape:
+        raise PccpError(PCCP_ERR_INVALID, "lb/ub must be contiguous and of the same shape")
+    n = lb.shape[0] if lb.dim() == 2 else 1
+    if lb.numel() != n * model.n_vars:
+        raise PccpError(PCCP_ERR_INVALID, "store width differs from the model's variables")
+    pinned = lb.is_pinned()
+    if status is None:
+        status = torch.empty(n, dtype=torch.int32, pin_memory=pinned)
+    if iterations is None:
+        iterations = torch.empty(n, dtype=torch.int32, pin_memory=pinned)
+    rc = pccp_propagate_host(model.handle, n, ctypes.c_void_p(lb.data_ptr()),
+                             ctypes.c_void_p(ub.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                             ctypes.c_void_p(iterations.data_ptr()), chunk_stores,
+                             _stream_ptr(stream))
+    check(rc, "pccp_propagate_host")
+    return status, iterations
 
 
 def _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,

@@ -77,6 +77,7 @@ SIGNATURES = {
     "pccp_model_get_info": (ctypes.c_int, [P, ctypes.POINTER(pccp_model_info)]),
     "pccp_propagate": (ctypes.c_int, [P, I32, P, P, P, P, P]),
     "pccp_propagate_ex": (ctypes.c_int, [P, I32, P, P, P, P, P, ctypes.POINTER(pccp_launch_config), P]),
+    "pccp_propagate_host": (ctypes.c_int, [P, I32, P, P, P, P, I32, P]),
     "pccp_solve": (ctypes.c_int, [P, ctypes.POINTER(pccp_solve_opts), ctypes.POINTER(pccp_result), P]),
     "pccp_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), I32, ctypes.POINTER(pccp_solve_opts),
                                         ctypes.POINTER(pccp_result), P]),

@@ -20,6 +20,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <unordered_map>
 #include <vector>
@@ -364,6 +365,8 @@ int policy_device(const pccp_policy* p);
 const PolicyDev* policy_dev(const pccp_policy* p);
 }  // namespace
 
+struct HostPipe;
+
 struct pccp_model {
   int device;
   int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective;
@@ -374,9 +377,13 @@ struct pccp_model {
   int32_t max_iter;  // every changing iteration narrows some bound by >= 1
   uint8_t* d_mem;    // image, then root int2[n_vars]
   int2* d_root;
+  HostPipe* pipe = nullptr;  // pccp_propagate_host's streams and slots (lazy)
+  std::mutex pipe_mu;               // one host-memory propagation at a time
 };
 
 namespace {
+
+void host_pipe_free(HostPipe* p);  // pccp_host.inc
 
 int64_t iabs64(int64_t x) { return x < 0 ? -x : x; }
 
@@ -1157,6 +1164,7 @@ void pccp_model_destroy(pccp_model* m) {
   cudaGetDevice(&prev);
   cudaSetDevice(m->device);
   cudaDeviceSynchronize();
+  host_pipe_free(m->pipe);
   cudaFree(m->d_mem);
   if (prev >= 0) cudaSetDevice(prev);
   delete m;
@@ -1629,3 +1637,4 @@ int pccp_solve(const pccp_model* m, const pccp_solve_opts* opts, pccp_result* re
 #include "pccp_noalloc.inc"
 #include "pccp_batch.inc"
 #include "pccp_policy.inc"
+#include "pccp_host.inc"

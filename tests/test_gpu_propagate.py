@@ -194,3 +194,25 @@ def test_store_size_limits():
     st, glb, gub, _ = run(m, lb, ub)
     x, f = compare_batch(om, lb, ub, st, glb, gub)
     assert x >= 2
+
+
+@pytest.mark.parametrize("pinned, chunk", [(True, 250), (True, 0), (False, 400)])
+def test_host_memory_pipeline_bit_exact(pinned, chunk):
+    """pccp_propagate_host: stores in host memory, copied in and out in chunks
+    (ragged last chunk) while other chunks propagate; results equal the
+    oracle's and the device entry point's."""
+    inst = config_instance("j30", 3)
+    m = pccp.Model.from_rcpsp(inst)
+    om = rcpsp_model(inst)
+    rows = pccp.rcpsp.build_rows(inst)
+    nodes = draw_partial_assignments(inst.n, inst.horizon, 600, seed=5)
+    lb, ub = pccp.rcpsp.node_stores(rows, nodes)
+    hlb, hub = torch.from_numpy(lb.copy()), torch.from_numpy(ub.copy())
+    if pinned:
+        hlb, hub = hlb.pin_memory(), hub.pin_memory()
+    st, it = pccp.propagate_host(m, hlb, hub, chunk_stores=chunk)
+    x, f = compare_batch(om, lb, ub, st.numpy(), hlb.numpy(), hub.numpy())
+    assert x > 100 and f > 10
+    dst, dlb, dub, dit = run(m, lb, ub)
+    assert np.array_equal(st.numpy(), dst) and np.array_equal(hlb.numpy()[st.numpy() == 0],
+                                                               dlb[dst == 0])
