@@ -965,7 +965,7 @@ struct PropPlan {
   void (*kern)(PropArgs);
   bool table_global;
   int stages;  // stream buffers per team (0: rows read in place)
-  int team, teams, grid;
+  int team, teams, grid, max_grid;
   size_t smem;
 };
 
@@ -1028,9 +1028,40 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   p->stages = stages;
   p->team = team;
   p->teams = teams;
-  p->grid = std::max(1, std::min(want, sms * per_sm));
+  p->max_grid = sms * per_sm;
+  p->grid = std::max(1, std::min(want, p->max_grid));
   p->smem = smem;
   return PCCP_OK;
+}
+
+// Queue one k_propagate launch of a plan over n_stores stores (>= 1), with
+// counter a zeroed device int; the grid shrinks for batches smaller than the
+// one planned.
+int launch_propagate(const pccp_model* m, const PropPlan& plan, int32_t n_stores, int32_t* lb,
+                     int32_t* ub, int32_t* status, int32_t* iterations, int32_t* work,
+                     const pccp_launch_config* cfg, int* counter, cudaStream_t s) {
+  PropArgs a;
+  a.image = m->d_mem;
+  a.root = m->d_root;
+  a.lb = lb;
+  a.ub = ub;
+  a.status = status;
+  a.iters = iterations;
+  a.counter = counter;
+  a.image_bytes = m->image_bytes;
+  a.n_vars = m->n_vars;
+  a.n_stores = n_stores;
+  a.team_size = plan.team;
+  a.teams = plan.teams;
+  a.max_iter = (cfg && cfg->max_iterations > 0) ? cfg->max_iterations : m->max_iter;
+  a.track_words = track_words(m->n_vars, m->n_lin);
+  a.work = work;
+  a.table_global = plan.table_global ? 1 : 0;
+  a.stream_stages = plan.stages;
+  a.reordered = m->reordered;
+  const int grid = std::max(1, std::min((n_stores + plan.teams - 1) / plan.teams, plan.max_grid));
+  plan.kern<<<grid, plan.team * plan.teams, plan.smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? PCCP_OK : PCCP_ERR_CUDA;
 }
 
 }  // namespace
@@ -1202,30 +1233,9 @@ int pccp_propagate_ex(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_
   int* counter = nullptr;
   PCCP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&counter), sizeof(int), s));
   PCCP_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
-  PropArgs a;
-  a.image = m->d_mem;
-  a.root = m->d_root;
-  a.lb = lb;
-  a.ub = ub;
-  a.status = status;
-  a.iters = iterations;
-  a.counter = counter;
-  a.image_bytes = m->image_bytes;
-  a.n_vars = m->n_vars;
-  a.n_stores = n_stores;
-  a.team_size = plan.team;
-  a.teams = plan.teams;
-  a.max_iter = (cfg && cfg->max_iterations > 0) ? cfg->max_iterations : m->max_iter;
-  a.track_words = track_words(m->n_vars, m->n_lin);
-  a.work = work;
-  a.table_global = plan.table_global ? 1 : 0;
-  a.stream_stages = plan.stages;
-  a.reordered = m->reordered;
-  plan.kern<<<plan.grid, plan.team * plan.teams, plan.smem, s>>>(a);
-  const cudaError_t le = cudaGetLastError();
+  rc = launch_propagate(m, plan, n_stores, lb, ub, status, iterations, work, cfg, counter, s);
   cudaFreeAsync(counter, s);
-  if (le != cudaSuccess) return PCCP_ERR_CUDA;
-  return PCCP_OK;
+  return rc;
 }
 
 int pccp_propagate(const pccp_model* m, int32_t n_stores, int32_t* lb, int32_t* ub,
