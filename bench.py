@@ -368,8 +368,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     cfg = None
     if explicit_launch(args):
-        cfg = pccp.launch_config(args.team, args.teams, args.ctas_per_sm, 0, args.skip_stable,
-                                 args.stream_table)
+        cfg = pccp.launch_config(args.team, args.teams, args.ctas_per_sm, 0,
+                                 True if args.skip_stable else None, args.stream_table)
 
     def prepare():
         lb.copy_(pristine_lb)

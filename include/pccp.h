@@ -151,8 +151,10 @@ typedef struct {
   int32_t ctas_per_sm;    /* cap on resident CTAs per SM used for the grid */
   int32_t max_iterations; /* per-store iteration budget (exceeded: PCCP_ERROR) */
   int32_t skip_stable;    /* 1: re-run a row only after one of its variables changed
-                             (change bitmaps per team; Sec. 6); 0: the eventless loop
-                             of Sec. 5.  Same fixed point either way. */
+                             (change bitmaps per team; Sec. 6); -1: the eventless loop
+                             of Sec. 5; 0: the library's choice (on for tables read
+                             from global memory, off for tables in shared memory).
+                             Same fixed point either way. */
   int32_t stream_table;   /* tables too large for shared memory: 0 read rows in place
                              (through L1/L2); 1 stream them through a ring of
                              shared-memory buffers by TMA bulk copies, segment by
@@ -218,8 +220,9 @@ typedef struct {
   int64_t time_limit_ms; /* stop after this many ms of device time (<= 0: none) */
   int32_t threads;       /* threads per team (multiple of 32, <= 1024; 0 = auto) */
   int32_t blocks;        /* CTAs for the parallel search (0 = auto) */
-  int32_t skip_stable;   /* as in pccp_launch_config; also lets a left child run
-                            only the rows of the decided variable first */
+  int32_t skip_stable;   /* as in pccp_launch_config (0: the library's choice); also
+                            lets a left child run only the rows of the decided
+                            variable first */
   int32_t stream_table;  /* as in pccp_launch_config */
   const pccp_policy* policy; /* required with PCCP_LEARNED, created on this device */
 } pccp_solve_opts;

@@ -219,12 +219,17 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _skip(skip_stable):
+    """None: the library's choice (0); True: 1; False: -1."""
+    return 0 if skip_stable is None else (1 if skip_stable else -1)
+
+
 def launch_config(team_threads=0, teams_per_cta=0, ctas_per_sm=0, max_iterations=0,
-                  skip_stable=False, stream_table=False):
+                  skip_stable=None, stream_table=False):
     """stream_table=True streams a table too large for shared memory through
     shared-memory buffers (TMA bulk copies) instead of reading it in place."""
     return _abi.pccp_launch_config(team_threads, teams_per_cta, ctas_per_sm, max_iterations,
-                                   int(bool(skip_stable)), int(bool(stream_table)))
+                                   _skip(skip_stable), int(bool(stream_table)))
 
 
 def propagate(model: Model, lb, ub, status=None, iterations=None, config=None, stream=None,
@@ -288,9 +293,9 @@ def propagate_host(model: Model, lb, ub, status=None, iterations=None, chunk_sto
 
 
 def _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
-          skip_stable=False, policy=None, stream_table=False):
+          skip_stable=None, policy=None, stream_table=False):
     return _abi.pccp_solve_opts(strategy, mode, int(bool(deterministic)), obj_ub, node_limit,
-                                time_limit_ms, threads, blocks, int(bool(skip_stable)),
+                                time_limit_ms, threads, blocks, _skip(skip_stable),
                                 int(bool(stream_table)),
                                 policy.handle if policy is not None else None)
 
@@ -306,7 +311,7 @@ def _result_dict(r, w):
 
 def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, deterministic=True,
           obj_ub=INT32_MAX, node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None,
-          skip_stable=False, policy=None, stream_table=False):
+          skip_stable=None, policy=None, stream_table=False):
     o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
               skip_stable, policy, stream_table)
     w = np.zeros(model.n_vars, dtype=np.int32)
@@ -319,7 +324,7 @@ def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, determini
 
 def solve_batch(models, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
                 node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None, noalloc=False,
-                skip_stable=False, policy=None, stream_table=False):
+                skip_stable=None, policy=None, stream_table=False):
     """Solve many models in one launch.  noalloc=True uses the allocation-free
     entry point (fixed device scratch; see include/pccp.h)."""
     o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, threads, blocks,
@@ -347,7 +352,7 @@ class Batch:
         self._ws = [np.zeros(m.n_vars, dtype=np.int32) for m in self.models]
 
     def solve_async(self, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
-                    node_limit=0, time_limit_ms=0, stream=None, skip_stable=False, policy=None):
+                    node_limit=0, time_limit_ms=0, stream=None, skip_stable=None, policy=None):
         o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, 0, 0, skip_stable,
                   policy)
         check(pccp_batch_solve_async(self.handle, o, _stream_ptr(stream)), "pccp_batch_solve_async")

@@ -903,14 +903,20 @@ int policy_x_words(const pccp_solve_opts* o, int max_branch) {
   return o->strategy == PCCP_LEARNED ? 8 * ((max_branch + 15) & ~15) : 0;
 }
 
+// skip_stable of the launch options: 1 on, -1 off, 0 the library's choice --
+// on for tables read from global memory (many iterations over a large table:
+// measured 17% faster on 120-task models), off for tables in shared memory
+// (the change bitmaps cost more than the rows they save there).
+bool use_skip_stable(int32_t opt, bool global) { return opt > 0 || (opt == 0 && global); }
+
 // The k_solve instantiation for a search's options (global: the tables are
 // read from global memory; stream: streamed through shared memory).
 using SolveKernel = void (*)(SolveArgs);
 template <bool kGlobal, bool kStream>
 SolveKernel solve_kernel_t(const pccp_solve_opts* o) {
   if (o->strategy == PCCP_LEARNED) return k_solve<false, true, kGlobal, kStream>;
-  return o->skip_stable ? k_solve<true, false, kGlobal, kStream>
-                        : k_solve<false, false, kGlobal, kStream>;
+  return use_skip_stable(o->skip_stable, kGlobal) ? k_solve<true, false, kGlobal, kStream>
+                                                  : k_solve<false, false, kGlobal, kStream>;
 }
 SolveKernel solve_kernel(const pccp_solve_opts* o, bool global, bool stream) {
   if (stream) return solve_kernel_t<true, true>(o);
@@ -998,7 +1004,7 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
                                                 per_team, teams, smem_max)
                             : 0;
   const size_t smem = base + static_cast<size_t>(teams) * (per_team + stream_bytes(stages));
-  const bool track = cfg && cfg->skip_stable;
+  const bool track = use_skip_stable(cfg ? cfg->skip_stable : 0, global);
   const auto kern =
       stages > 0 ? (track ? k_propagate<1024, 1, true, true, true>
                           : k_propagate<1024, 1, false, true, true>)
@@ -1438,11 +1444,11 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   using EpsKernel = void (*)(EpsArgs);
   EpsKernel kexp, ksol;
   if (stages > 0)
-    eps_kernels<true, true>(learned, o->skip_stable, &kexp, &ksol);
+    eps_kernels<true, true>(learned, use_skip_stable(o->skip_stable, true), &kexp, &ksol);
   else if (global)
-    eps_kernels<true, false>(learned, o->skip_stable, &kexp, &ksol);
+    eps_kernels<true, false>(learned, use_skip_stable(o->skip_stable, true), &kexp, &ksol);
   else
-    eps_kernels<false, false>(learned, o->skip_stable, &kexp, &ksol);
+    eps_kernels<false, false>(learned, use_skip_stable(o->skip_stable, false), &kexp, &ksol);
   PCCP_CUDA(cudaFuncSetAttribute(kexp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
   PCCP_CUDA(cudaFuncSetAttribute(ksol, cudaFuncAttributeMaxDynamicSharedMemorySize,
