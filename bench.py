@@ -244,10 +244,16 @@ def profile_path():
 
 
 def kernel_hash():
+    """Hash of the propagation kernel's sources with comments and blank lines
+    left out (a comment edit does not make a capture stale)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, p), "rb").read())
+        for line in open(os.path.join(ROOT, p)).read().splitlines():
+            code = re.sub(r"//.*$", "", line).rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

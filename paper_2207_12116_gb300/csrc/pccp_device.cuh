@@ -657,12 +657,16 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
 // One full evaluation of every row of the table (one iteration of the
 // eventless loop).  Rows of one kind run back to back so warps stay uniform:
 // a thread per reified, temporal and short linear row, a warp per long
-// linear row.  Kind order linear, reified, temporal: of the six orders this
-// one needs the fewest iterations on the scheduling models (the order never
-// changes the fixed point, Sec. 3).
+// linear row.  Kind order reified, temporal, linear (the order never
+// changes the fixed point, Sec. 3): linear first saves a few iterations on
+// 120-task models but costs the depth-first searches of 30-task models more.
 template <bool kTrack, bool kQuiet>
 __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags& f) {
   const Tab& tb = w.tb;
+  for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr)
+    eval_reified_pair<kTrack, kQuiet>(w, tb.rfp[r], f);
+  for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack, kQuiet>(w, tb.rf[r], f);
+  for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
   for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) {
     if (skip_linear_short<kTrack>(w, r, f)) continue;
     const int4 h = tb.lin[r];
@@ -673,10 +677,6 @@ __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags
     const int4 h = tb.lin_long[r];
     eval_linear_warp_at<kTrack>(w, h, tb.terms_long + h.y, tm.lane, f);
   }
-  for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr)
-    eval_reified_pair<kTrack, kQuiet>(w, tb.rfp[r], f);
-  for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack, kQuiet>(w, tb.rf[r], f);
-  for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
 }
 
 // ------------------------------------------------------------ streamed sweep
