@@ -439,7 +439,7 @@ def run_gpu(args):
             flush.fill_(1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            pccp.propagate_host(model, lb_pin, ub_pin, out_st, out_it)
+            pccp.propagate_host(model, lb_pin, ub_pin, out_st, out_it, chunk_stores=args.e2e_chunk)
             dt = time.perf_counter() - t0
             if k >= args.warmup:
                 e2e_ms.append(dt * 1000.0)
@@ -652,6 +652,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunk", type=int, default=0,
+                    help="stores per chunk of the end-to-end call (0: the library's default)")
     ap.add_argument("--no-search", action="store_true")
     ap.add_argument("--learned", action="store_true",
                     help="learned branching vs first-fail on 64 60-task models (own JSON line)")

@@ -176,7 +176,7 @@ int pccp_propagate_ex(const pccp_model* model, int32_t n_stores, int32_t* lb, in
 /* pccp_propagate for stores that live in HOST memory: lb, ub are HOST int32
  * [n_stores][n_vars], updated in place with the fixed points; status and
  * iterations (may be NULL) are HOST int32 [n_stores].  The stores travel in
- * chunks of chunk_stores (<= 0: the whole batch as one chunk):
+ * chunks of chunk_stores (<= 0: four chunks of at least 2,048 stores):
  * while one chunk is propagated on `stream`, the next is copied in and the
  * previous one copied out on two streams of the model's own, through two
  * device slots.  Streams, events and slots are created on the model's first
