@@ -21,8 +21,11 @@ def test_j120_table_exceeds_shared_memory():
     assert m.info.table_bytes > 232448  # larger than one CTA's shared memory
 
 
-@pytest.mark.parametrize("stream_table", [True, False])
-def test_j120_propagation_bit_exact(stream_table):
+@pytest.mark.parametrize("stream_table, skip_stable", [(True, None), (False, None),
+                                                       (False, False), (True, False)])
+def test_j120_propagation_bit_exact(stream_table, skip_stable):
+    """Tables in global memory: read in place or streamed, with stable rows
+    skipped (the default there) or every row every iteration."""
     inst = config_instance("j120", 0)
     rows = pccp.rcpsp.build_rows(inst)
     m = pccp.Model.from_rows(rows)
@@ -32,17 +35,19 @@ def test_j120_propagation_bit_exact(stream_table):
     nodes = [[]] + draw_partial_assignments(inst.n, inst.horizon, 11, seed=21)
     lb, ub = pccp.rcpsp.node_stores(rows, nodes)
     dlb, dub = torch.from_numpy(lb).cuda(), torch.from_numpy(ub).cuda()
-    st, it = pccp.propagate(m, dlb, dub, config=pccp.launch_config(stream_table=stream_table))
+    cfg = pccp.launch_config(stream_table=stream_table, skip_stable=skip_stable)
+    st, it = pccp.propagate(m, dlb, dub, config=cfg)
     torch.cuda.synchronize()
     x, f = compare_batch(om, lb, ub, st.cpu().numpy(), dlb.cpu().numpy(), dub.cpu().numpy())
     assert x >= 5
 
 
-@pytest.mark.parametrize("stream_table", [True, False])
-def test_j120_search_matches_oracle_node_limited(stream_table):
+@pytest.mark.parametrize("stream_table, skip_stable", [(True, None), (False, None),
+                                                       (False, False)])
+def test_j120_search_matches_oracle_node_limited(stream_table, skip_stable):
     inst = config_instance("j120", 1)
     r = pccp.solve_batch([pccp.Model.from_rcpsp(inst)], node_limit=12,
-                         stream_table=stream_table)[0]
+                         stream_table=stream_table, skip_stable=skip_stable)[0]
     o = oracle.solve(rcpsp_model(inst), node_limit=12)
     assert (r["nodes"], r["fails"], r["solutions"], r["status"]) == \
         (o["nodes"], o["fails"], o["solutions"], pccp.PCCP_RES_LIMIT)
@@ -129,8 +134,9 @@ def big_generic_stores(lb0, ub0, linear):
     return lb, ub
 
 
-@pytest.mark.parametrize("stream_table", [True, False])
-def test_streamed_segments_of_every_kind_bit_exact(stream_table):
+@pytest.mark.parametrize("stream_table, skip_stable", [(True, None), (False, None),
+                                                       (False, False), (True, False)])
+def test_streamed_segments_of_every_kind_bit_exact(stream_table, skip_stable):
     lb0, ub0, temporal, linear, reified = big_generic_model(5)
     m = pccp.Model.from_lists(lb0, ub0, temporal, linear, reified, -1, list(range(3000)))
     assert m.info.table_bytes + 8 * m.n_vars > 232448  # read from global memory
@@ -139,7 +145,8 @@ def test_streamed_segments_of_every_kind_bit_exact(stream_table):
     om = oracle.Model(lb0, ub0, temporal, linear, reified, -1, list(range(3000)))
     lb, ub = big_generic_stores(lb0, ub0, linear)
     dlb, dub = torch.from_numpy(lb).cuda(), torch.from_numpy(ub).cuda()
-    st, it = pccp.propagate(m, dlb, dub, config=pccp.launch_config(stream_table=stream_table))
+    cfg = pccp.launch_config(stream_table=stream_table, skip_stable=skip_stable)
+    st, it = pccp.propagate(m, dlb, dub, config=cfg)
     torch.cuda.synchronize()
     x, f = compare_batch(om, lb, ub, st.cpu().numpy(), dlb.cpu().numpy(), dub.cpu().numpy())
     assert x >= 3
