@@ -657,25 +657,44 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
 // One full evaluation of every row of the table (one iteration of the
 // eventless loop).  Rows of one kind run back to back so warps stay uniform:
 // a thread per reified, temporal and short linear row, a warp per long
-// linear row.  Kind order reified, temporal, linear (the order never
-// changes the fixed point, Sec. 3): linear first saves a few iterations on
-// 120-task models but costs the depth-first searches of 30-task models more.
+// linear row.  Kind order (it never changes the fixed point, Sec. 3): with
+// the table in shared memory reified, temporal, linear; in global memory
+// linear, reified, temporal -- each the faster of the six orders measured
+// there (the second saves iterations on 120-task models, the first is
+// faster for the depth-first searches of 30-task models).
 template <bool kTrack, bool kQuiet>
 __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags& f) {
   const Tab& tb = w.tb;
-  for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr)
-    eval_reified_pair<kTrack, kQuiet>(w, tb.rfp[r], f);
-  for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack, kQuiet>(w, tb.rf[r], f);
-  for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
-  for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) {
-    if (skip_linear_short<kTrack>(w, r, f)) continue;
-    const int4 h = tb.lin[r];
-    eval_linear_thread_at<kTrack>(w, h, tb.terms + h.y, f);
-  }
-  for (int r = tm.warp; r < tb.n_lin_long; r += tm.nwarps) {
-    if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
-    const int4 h = tb.lin_long[r];
-    eval_linear_warp_at<kTrack>(w, h, tb.terms_long + h.y, tm.lane, f);
+  if (kQuiet) {  // tables in global memory: linear, reified, temporal
+    for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) {
+      if (skip_linear_short<kTrack>(w, r, f)) continue;
+      const int4 h = tb.lin[r];
+      eval_linear_thread_at<kTrack>(w, h, tb.terms + h.y, f);
+    }
+    for (int r = tm.warp; r < tb.n_lin_long; r += tm.nwarps) {
+      if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
+      const int4 h = tb.lin_long[r];
+      eval_linear_warp_at<kTrack>(w, h, tb.terms_long + h.y, tm.lane, f);
+    }
+    for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr)
+      eval_reified_pair<kTrack, kQuiet>(w, tb.rfp[r], f);
+    for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack, kQuiet>(w, tb.rf[r], f);
+    for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
+  } else {  // tables in shared memory: reified, temporal, linear
+    for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr)
+      eval_reified_pair<kTrack, kQuiet>(w, tb.rfp[r], f);
+    for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack, kQuiet>(w, tb.rf[r], f);
+    for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
+    for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) {
+      if (skip_linear_short<kTrack>(w, r, f)) continue;
+      const int4 h = tb.lin[r];
+      eval_linear_thread_at<kTrack>(w, h, tb.terms + h.y, f);
+    }
+    for (int r = tm.warp; r < tb.n_lin_long; r += tm.nwarps) {
+      if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
+      const int4 h = tb.lin_long[r];
+      eval_linear_warp_at<kTrack>(w, h, tb.terms_long + h.y, tm.lane, f);
+    }
   }
 }
 
