@@ -425,16 +425,12 @@ int warp_wavefronts(const int32_t* vars, int n, const std::vector<int32_t>& iof)
       words[nw++] = w;
       words[nw++] = w + 1;
     }
+    std::sort(words, words + nw);
+    int per_bank[32] = {0};
     int worst = 0;
-    for (int b = 0; b < 32; ++b) {
-      int distinct = 0;
-      for (int i = 0; i < nw; ++i) {
-        if (words[i] % 32 != static_cast<uint32_t>(b)) continue;
-        bool seen = false;
-        for (int j = 0; j < i; ++j) seen = seen || words[j] == words[i];
-        distinct += seen ? 0 : 1;
-      }
-      worst = std::max(worst, distinct);
+    for (int i = 0; i < nw; ++i) {
+      if (i > 0 && words[i] == words[i - 1]) continue;  // one word, one access
+      worst = std::max(worst, ++per_bank[words[i] % 32]);
     }
     total += worst;
   }
