@@ -97,12 +97,15 @@ typedef struct pccp_model pccp_model; /* opaque; owns a device copy of the table
 
 /* Validates `desc`, packs its rows into the structure-of-arrays propagator
  * table (the guarded normal form of Sec. 3) and copies it to the current
- * device (synchronously).  On success *out receives a model that must be
- * released with pccp_model_destroy.  Errors: INVALID, OVERFLOW, UNSUPPORTED,
- * CUDA (then *out is NULL). */
+ * device (synchronously).  The library may keep the variables in shared
+ * memory in an order of its own (pccp_model_info.reordered); every array a
+ * call reads or writes stays in the order of `desc`.  On success *out
+ * receives a model that must be released with pccp_model_destroy.  Errors:
+ * INVALID, OVERFLOW, UNSUPPORTED, CUDA (then *out is NULL). */
 int pccp_model_create(const pccp_model_desc* desc, pccp_model** out);
 
-/* Frees the model and its device table (synchronises the device first).
+/* Frees the model, its device table and the buffers of pccp_propagate_host
+ * (synchronises the device first).  No call on the model may be in progress.
  * NULL is accepted. */
 void pccp_model_destroy(pccp_model* model);
 
@@ -110,10 +113,13 @@ void pccp_model_destroy(pccp_model* model);
 typedef struct {
   int32_t n_vars;
   int32_t n_temporal, n_linear, n_terms, n_reified;
-  int32_t table_bytes;      /* packed table copied to shared memory per CTA */
+  int32_t table_bytes;      /* packed table, copied to shared memory per CTA when it
+                               fits beside a store (else read from global memory) */
   int64_t bytes_per_sweep;  /* algorithmic bytes of one evaluation of every row:
                                temporal 20, reified 40, linear 12 + 12 * len */
-  int32_t max_store_vars;   /* largest n_vars a single CTA can stage */
+  int32_t max_store_vars;   /* largest n_vars a single CTA can stage beside the table
+                               (stores of more variables read the table from global
+                               memory, down to the shared-memory limit of one store) */
   int32_t n_segments;       /* byte ranges of whole rows (<= 32 KB each) that one sweep
                                streams when the table is read from global memory */
   int32_t reordered;        /* 1: the library keeps the variables in shared memory in
@@ -132,8 +138,9 @@ int pccp_model_get_info(const pccp_model* model, pccp_model_info* info);
  *   status     : DEVICE int32 [n_stores]: PCCP_FIXPOINT / PCCP_FAILED /
  *                PCCP_ERROR.  lb/ub of a non-FIXPOINT store are unspecified.
  *   iterations : DEVICE int32 [n_stores] or NULL: fixed-point iterations run
- *                for each store (every row is evaluated once per iteration;
- *                the loop is eventless, Sec. 5).
+ *                for each store (with the table in shared memory every row
+ *                is evaluated once per iteration, the eventless loop of
+ *                Sec. 5; see skip_stable in pccp_launch_config).
  *   n_stores   : >= 0 (0 queues nothing).
  * Asynchronous on `stream`.  Errors: INVALID, SMEM, CUDA.
  * Calls on one model may run concurrently on different streams. */
