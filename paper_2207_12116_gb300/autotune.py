@@ -13,8 +13,8 @@ import statistics
 
 from . import Model, launch_config, propagate, solve_batch, PccpError
 
-PROPAGATE_CANDIDATES = [(64, 4), (64, 8), (96, 5), (128, 2), (128, 4), (128, 8), (160, 3),
-                        (256, 2), (256, 4), (512, 1)]
+PROPAGATE_CANDIDATES = [(64, 4), (64, 8), (64, 15), (96, 5), (96, 10), (128, 2), (128, 4),
+                        (128, 8), (160, 3), (192, 5), (256, 2), (256, 4), (512, 1)]
 SEARCH_THREADS = [64, 128, 256, 512]
 
 _cache = {}
