@@ -338,6 +338,40 @@ def search_bench(pccp, cpu=True):
     return out
 
 
+def link_probe(nbytes, reps=5):
+    """The CPU-GPU link as the host pipeline uses it: copy-engine copies of
+    nbytes between pinned host memory and the device, host to device, device
+    to host, and both at once on two streams (best of reps, CUDA events)."""
+    import torch
+    n = nbytes // 4
+    h_in = torch.ones(n, dtype=torch.int32).pin_memory()
+    h_out = torch.empty(n, dtype=torch.int32).pin_memory()
+    d_in = torch.empty(n, dtype=torch.int32, device="cuda")
+    d_out = torch.ones(n, dtype=torch.int32, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    best = {"h2d": 1e9, "d2h": 1e9, "both": 1e9}
+    for _ in range(reps):
+        for kind in best:
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s1)
+            s2.wait_event(a)
+            if kind in ("h2d", "both"):
+                with torch.cuda.stream(s1):
+                    d_in.copy_(h_in, non_blocking=True)
+            if kind in ("d2h", "both"):
+                with torch.cuda.stream(s2):
+                    h_out.copy_(d_out, non_blocking=True)
+            c = torch.cuda.Event()
+            c.record(s2)
+            s1.wait_event(c)
+            b.record(s1)
+            b.synchronize()
+            best[kind] = min(best[kind], a.elapsed_time(b))
+    return {"h2d_gbs": 4 * n / best["h2d"] / 1e6, "d2h_gbs": 4 * n / best["d2h"] / 1e6,
+            "both_gbs": 8 * n / best["both"] / 1e6, "bytes_each_way": 4 * n}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -423,8 +457,9 @@ def run_gpu(args):
         if cfg is not None:
             raise SystemExit("--no-e2e is required with an explicit launch shape")
         # end to end through the public API (pccp_propagate_host): pinned host
-        # stores in, fixed points out, the copies of one chunk overlapping the
-        # propagation of another; wall time of each synchronous call
+        # stores in, fixed points out, copied in chunks that overlap the
+        # propagation of other chunks (--e2e-chunk -1: read and written in
+        # place by the kernel); wall time of each synchronous call
         src_lb = torch.from_numpy(lb_h)
         src_ub = torch.from_numpy(ub_h)
         lb_pin = torch.empty_like(src_lb).pin_memory()
@@ -449,8 +484,22 @@ def run_gpu(args):
         assert np.array_equal(lb_pin.numpy()[fx], lb.cpu().numpy()[fx]), "end-to-end stores differ"
         e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * nv * N_NODES,
                "d2h_bytes_per_step": 2 * 4 * nv * N_NODES + 8 * N_NODES,
-               "api": "pccp_propagate_host (pinned host stores, chunked copy/compute overlap)",
+               "api": ("pccp_propagate_host (pinned host stores read and written in place by "
+                       "the kernel over the CPU-GPU link)" if args.e2e_chunk < 0 else
+                       "pccp_propagate_host (pinned host stores, copied in chunks of "
+                       + (f"{args.e2e_chunk}" if args.e2e_chunk else "the library's size")
+                       + " overlapping the propagation)"),
                "timing": "host wall clock around each synchronous call"}
+        if not args.no_probes:
+            # the roof of this path: every store crosses the CPU-GPU link twice
+            lk = link_probe(4 * nv * N_NODES)
+            step_bytes = e2e["h2d_bytes_per_step"] + e2e["d2h_bytes_per_step"]
+            link_gbs = step_bytes / (statistics.mean(e2e_ms) / 1000) / 1e9
+            e2e["link"] = {"bound": "cpu-gpu link", "achieved": link_gbs, "peak": lk["both_gbs"],
+                           "unit": "GB/s", "frac": link_gbs / lk["both_gbs"],
+                           "peak_source": "measured in this run: copy-engine copies of "
+                                          f"{lk['bytes_each_way']} B each way at once, pinned",
+                           "h2d_gbs": lk["h2d_gbs"], "d2h_gbs": lk["d2h_gbs"]}
 
     if rank == 0:
         peaks = load_peaks()
@@ -653,7 +702,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-chunk", type=int, default=0,
-                    help="stores per chunk of the end-to-end call (0: the library's default)")
+                    help="stores per chunk of the end-to-end call (0: the library's choice; "
+                         "-1: no copies, the kernel reads and writes the host stores)")
     ap.add_argument("--no-search", action="store_true")
     ap.add_argument("--learned", action="store_true",
                     help="learned branching vs first-fail on 64 60-task models (own JSON line)")

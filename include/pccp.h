@@ -182,18 +182,34 @@ int pccp_propagate_ex(const pccp_model* model, int32_t n_stores, int32_t* lb, in
 
 /* pccp_propagate for stores that live in HOST memory: lb, ub are HOST int32
  * [n_stores][n_vars], updated in place with the fixed points; status and
- * iterations (may be NULL) are HOST int32 [n_stores].  The stores travel in
- * chunks of chunk_stores (<= 0: four chunks of at least 2,048 stores):
- * while one chunk is propagated on `stream`, the next is copied in and the
- * previous one copied out on two streams of the model's own, through two
- * device slots.  Streams, events and slots are created on the model's first
- * such call, grown for larger chunks and freed with the model; calls on one
- * model are serialised (the host thread waits for the one in progress).
- * Page-locked host memory (cudaHostAlloc, cudaHostRegister, a pinned torch
- * tensor) lets the copies overlap; pageable memory works but serialises
- * them.  The copies start after the work already queued on `stream`, and
- * later work on `stream` follows them.  Synchronous: returns once every
- * result is in host memory.  Errors: INVALID, SMEM, CUDA. */
+ * iterations (may be NULL) are HOST int32 [n_stores].  Two ways to move the
+ * stores, chosen by chunk_stores:
+ *   > 0                : chunked copies, chunk_stores stores per chunk;
+ *   0                  : chunked copies, about four chunks, each a whole
+ *                        number of stores per team of the GPU (the fastest
+ *                        measured);
+ *   PCCP_HOST_IN_PLACE : no copies: one launch whose teams read their stores
+ *                        from host memory and write the fixed points, status
+ *                        and iterations back there, over the CPU-GPU link.
+ *                        Every array must be page-locked and mapped into the
+ *                        device's address space (cudaHostAlloc,
+ *                        cudaHostRegister with mapping, a pinned torch tensor:
+ *                        with unified addressing all of these are), each one
+ *                        allocation; the mapping is checked at both ends of
+ *                        each array and INVALID returned if it is missing.
+ * Chunked, while one chunk is propagated the next chunks are copied in and
+ * the previous ones copied out, on three streams of the model's own (copy
+ * in, propagate, copy out) through up to four device slots (page-locked
+ * memory lets the copies overlap; pageable memory works but serialises
+ * them); status and iterations, when mapped as above, are written by the
+ * kernels where they lie instead of being copied.  Streams, events and
+ * slots are created on the model's first such call, grown for larger chunks
+ * and freed with the model; calls on one model are serialised (the host
+ * thread waits for the one in progress).  Either way the transfers start
+ * after the work already queued on `stream`, and later work on `stream`
+ * follows them.  Synchronous: returns once every result is in host memory.
+ * Errors: INVALID (also chunk_stores < PCCP_HOST_IN_PLACE), SMEM, CUDA. */
+#define PCCP_HOST_IN_PLACE (-1)
 int pccp_propagate_host(const pccp_model* model, int32_t n_stores, int32_t* lb, int32_t* ub,
                         int32_t* status, int32_t* iterations, int32_t chunk_stores,
                         void* stream);

@@ -20,7 +20,7 @@ from ._abi import (PCCP_OK, PCCP_ERR_INVALID, PCCP_ERR_OVERFLOW, PCCP_ERR_SMEM, 
                    PCCP_FAILED, PCCP_ERROR, PCCP_INPUT_ORDER, PCCP_FIRST_FAIL, PCCP_LEARNED,
                    PCCP_OPTIMISE,
                    PCCP_COUNT_ALL, PCCP_RES_OPTIMAL, PCCP_RES_INFEASIBLE, PCCP_RES_LIMIT,
-                   INT32_MAX, PccpError, check, load, library_path)
+                   PCCP_HOST_IN_PLACE, INT32_MAX, PccpError, check, load, library_path)
 from . import rcpsp  # noqa: F401
 
 __all__ = ["Model", "pccp_model_create", "pccp_model_destroy", "pccp_model_get_info",
@@ -267,10 +267,13 @@ def pccp_propagate_host(handle, n_stores, lb_ptr, ub_ptr, status_ptr, iters_ptr,
 
 def propagate_host(model: Model, lb, ub, status=None, iterations=None, chunk_stores=0,
                    stream=None):
-    """End-to-end form (pccp_propagate_host): HOST int32 tensors [n, n_vars]
-    (pin them, e.g. torch.empty(..., pin_memory=True), for copies that
-    overlap the propagation), updated in place with the fixed points.
-    Returns (status, iterations), host int32 tensors [n]."""
+    """End-to-end form (pccp_propagate_host): HOST int32 tensors [n, n_vars],
+    updated in place with the fixed points.  chunk_stores 0 (the library's
+    chunking) or > 0 copies them through device slots in chunks that overlap
+    the propagation (pin them, e.g. torch.empty(..., pin_memory=True), for
+    the overlap); PCCP_HOST_IN_PLACE has the kernel read and write pinned
+    tensors where they lie.  Returns (status, iterations), host int32
+    tensors [n]."""
     import torch
     if lb.dtype != torch.int32 or ub.dtype != torch.int32 or lb.is_cuda or ub.is_cuda:
         raise PccpError(PCCP_ERR_INVALID, "lb/ub must be int32 host tensors")

@@ -25,6 +25,8 @@ PCCP_FIXPOINT, PCCP_FAILED, PCCP_ERROR = 0, 1, 2
 PCCP_INPUT_ORDER, PCCP_FIRST_FAIL, PCCP_LEARNED = 0, 1, 2
 PCCP_OPTIMISE, PCCP_COUNT_ALL = 0, 1
 PCCP_RES_OPTIMAL, PCCP_RES_INFEASIBLE, PCCP_RES_LIMIT = 0, 1, 2
+PCCP_HOST_IN_PLACE = -1
+PCCP_NOALLOC_SCRATCH_BYTES = 8 << 20
 INT32_MAX = (1 << 31) - 1
 
 P = ctypes.c_void_p

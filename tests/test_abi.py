@@ -28,6 +28,21 @@ def test_library_exports_every_declared_entry_point():
         assert n in _abi.SIGNATURES, f"binding lacks {n}"
 
 
+def test_binding_constants_match_the_headers():
+    """Every integer #define of the headers has the same value in the binding."""
+    seen = 0
+    for header in ("pccp.h", "pccp_probe.h"):
+        text = open(os.path.join(ROOT, "include", header)).read()
+        for name, val in re.findall(r"^#define[ \t]+(PCCP_[A-Z0-9_]+)[ \t]+(.+?)[ \t]*(?:/\*.*)?$", text,
+                                    flags=re.M):
+            m = re.fullmatch(r"\(?(-?\d+)u?(?:\s*<<\s*(\d+))?\)?", val)
+            assert m, (name, val)
+            want = int(m.group(1)) << int(m.group(2) or 0)
+            assert getattr(_abi, name) == want, name
+            seen += 1
+    assert seen >= 20
+
+
 def test_probe_library_exports_every_declared_entry_point():
     lib = _abi.load_probe()
     names = declared_functions("pccp_probe.h")

@@ -196,11 +196,13 @@ def test_store_size_limits():
     assert x >= 2
 
 
-@pytest.mark.parametrize("pinned, chunk", [(True, 250), (True, 0), (False, 400)])
+@pytest.mark.parametrize("pinned, chunk", [(True, 250), (True, 0), (False, 400), (False, 0),
+                                           (True, pccp.PCCP_HOST_IN_PLACE)])
 def test_host_memory_pipeline_bit_exact(pinned, chunk):
     """pccp_propagate_host: stores in host memory, copied in and out in chunks
-    (ragged last chunk) while other chunks propagate; results equal the
-    oracle's and the device entry point's."""
+    (ragged last chunk) while other chunks propagate, or read and written in
+    place by the kernel (PCCP_HOST_IN_PLACE); results equal the oracle's and
+    the device entry point's."""
     inst = config_instance("j30", 3)
     m = pccp.Model.from_rcpsp(inst)
     om = rcpsp_model(inst)
@@ -216,3 +218,49 @@ def test_host_memory_pipeline_bit_exact(pinned, chunk):
     dst, dlb, dub, dit = run(m, lb, ub)
     assert np.array_equal(st.numpy(), dst) and np.array_equal(hlb.numpy()[st.numpy() == 0],
                                                                dlb[dst == 0])
+
+
+def test_host_in_place_needs_mapped_memory():
+    inst = config_instance("j30", 3)
+    m = pccp.Model.from_rcpsp(inst)
+    lb = torch.tensor(m.lb0, dtype=torch.int32)[None].repeat(8, 1)
+    ub = torch.tensor(m.ub0, dtype=torch.int32)[None].repeat(8, 1)
+    for chunk in (pccp.PCCP_HOST_IN_PLACE, -2):
+        with pytest.raises(pccp.PccpError) as e:
+            pccp.propagate_host(m, lb.clone(), ub.clone(), chunk_stores=chunk)
+        assert e.value.code == pccp.PCCP_ERR_INVALID
+    # the chunked copies take any mix of pinned and pageable arrays
+    plb, pub = lb.clone().pin_memory(), ub.clone().pin_memory()
+    st = torch.empty(8, dtype=torch.int32)
+    pccp.propagate_host(m, plb, pub, status=st)
+    with pytest.raises(pccp.PccpError):
+        pccp.propagate_host(m, lb.clone().pin_memory(), ub.clone().pin_memory(), status=st,
+                            chunk_stores=pccp.PCCP_HOST_IN_PLACE)
+    dst, dlb, dub, _ = run(m, lb.numpy(), ub.numpy())
+    assert np.array_equal(st.numpy(), dst) and np.array_equal(plb.numpy()[dst == 0], dlb[dst == 0])
+
+
+@pytest.mark.parametrize("family, n_nodes", [("tiny8", 300), ("j120", 48)])
+def test_host_in_place_reordered_and_global_tables(family, n_nodes):
+    """In place on a model kept in the library's own variable order (staging
+    through the variable map) and on a 120-task model whose table is read
+    from global memory: equal to the device entry point, and to the oracle
+    on the stores it checks."""
+    inst = config_instance(family, 0)
+    m = pccp.Model.from_rcpsp(inst)
+    if family == "tiny8":
+        assert m.info.reordered == 1
+    rows = pccp.rcpsp.build_rows(inst)
+    nodes = draw_partial_assignments(inst.n, inst.horizon, n_nodes, seed=11)
+    lb, ub = pccp.rcpsp.node_stores(rows, nodes)
+    hlb, hub = torch.from_numpy(lb.copy()).pin_memory(), torch.from_numpy(ub.copy()).pin_memory()
+    st, it = pccp.propagate_host(m, hlb, hub, chunk_stores=pccp.PCCP_HOST_IN_PLACE)
+    dst, dlb, dub, dit = run(m, lb, ub)
+    # (iteration counts depend on the interleaving of the tells: not compared)
+    assert np.array_equal(st.numpy(), dst) and (it.numpy()[dst == 0] >= 1).all()
+    fx = dst == 0
+    assert np.array_equal(hlb.numpy()[fx], dlb[fx]) and np.array_equal(hub.numpy()[fx], dub[fx])
+    om = rcpsp_model(inst)
+    sample = range(n_nodes) if family == "tiny8" else range(0, n_nodes, 12)
+    x, f = compare_batch(om, lb, ub, st.numpy(), hlb.numpy(), hub.numpy(), rows=sample)
+    assert x + f == len(sample)
