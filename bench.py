@@ -492,7 +492,7 @@ def run_gpu(args):
                "timing": "host wall clock around each synchronous call"}
         if not args.no_probes:
             # the roof of this path: every store crosses the CPU-GPU link twice
-            lk = link_probe(4 * nv * N_NODES)
+            lk = link_probe(8 * nv * N_NODES)  # lb and ub, each way
             step_bytes = e2e["h2d_bytes_per_step"] + e2e["d2h_bytes_per_step"]
             link_gbs = step_bytes / (statistics.mean(e2e_ms) / 1000) / 1e9
             e2e["link"] = {"bound": "cpu-gpu link", "achieved": link_gbs, "peak": lk["both_gbs"],
