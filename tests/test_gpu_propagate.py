@@ -264,3 +264,26 @@ def test_host_in_place_reordered_and_global_tables(family, n_nodes):
     sample = range(n_nodes) if family == "tiny8" else range(0, n_nodes, 12)
     x, f = compare_batch(om, lb, ub, st.numpy(), hlb.numpy(), hub.numpy(), rows=sample)
     assert x + f == len(sample)
+
+
+def test_host_default_chunking_large_batch():
+    """10,000 stores through the default chunking (a one-store-per-team first
+    chunk, then chunks of two stores per team, four slots reused): equal to
+    the device entry point everywhere and to the oracle on stores around
+    every chunk boundary."""
+    inst = config_instance("j30", 0)
+    m = pccp.Model.from_rcpsp(inst)
+    rows = pccp.rcpsp.build_rows(inst)
+    nodes = draw_partial_assignments(inst.n, inst.horizon, 10_000, seed=21)
+    lb, ub = pccp.rcpsp.node_stores(rows, nodes)
+    hlb, hub = torch.from_numpy(lb.copy()).pin_memory(), torch.from_numpy(ub.copy()).pin_memory()
+    st, it = pccp.propagate_host(m, hlb, hub)
+    dst, dlb, dub, _ = run(m, lb, ub)
+    fx = dst == 0
+    assert np.array_equal(st.numpy(), dst)
+    assert np.array_equal(hlb.numpy()[fx], dlb[fx]) and np.array_equal(hub.numpy()[fx], dub[fx])
+    assert (it.numpy()[fx] >= 1).all()
+    sample = sorted({i for b in range(0, 10_001, 608) for i in (b - 1, b) if 0 <= i < 10_000})
+    x, f = compare_batch(rcpsp_model(inst), lb, ub, st.numpy(), hlb.numpy(), hub.numpy(),
+                         rows=sample)
+    assert x + f == len(sample)
