@@ -4,8 +4,8 @@
  *
  * The method itself has no counterpart here: the paper's Sec. 5 names cache
  * use (shared memory per block) as the design driver of its GPU layout but
- * gives no roofline.  These probes give the denominators against which the
- * library's kernels are judged:
+ * gives no roofline.  These probes measure the denominators of the library's
+ * roofline fractions:
  *  - shared-memory load bandwidth (128 bytes per clock per SM nominal), the
  *    bound of propagation when table and stores are resident in shared memory;
  *  - the throughput of the relaxed CTA-scope shared atomics that carry every
