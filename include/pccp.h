@@ -185,8 +185,9 @@ int pccp_propagate_ex(const pccp_model* model, int32_t n_stores, int32_t* lb, in
  * iterations (may be NULL) are HOST int32 [n_stores].  Two ways to move the
  * stores, chosen by chunk_stores:
  *   > 0                : chunked copies, chunk_stores stores per chunk;
- *   0                  : chunked copies, about four chunks, each a whole
- *                        number of stores per team of the GPU (the fastest
+ *   0                  : chunked copies: a first chunk of one store per
+ *                        team of the GPU, then about four chunks, each a
+ *                        whole number of stores per team (the fastest
  *                        measured);
  *   PCCP_HOST_IN_PLACE : no copies: one launch whose teams read their stores
  *                        from host memory and write the fixed points, status
