@@ -949,6 +949,24 @@ int sm_count() {
   return v;
 }
 
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `smem`.  Limits only grow, so a plan made on another host thread for
+// a smaller model cannot lower the limit between this plan and its launch.
+cudaError_t allow_smem(const void* kern, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<uint64_t, std::unordered_map<const void*, size_t>> set;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = set[static_cast<uint64_t>(dev)][kern];
+  if (cur >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem));
+  if (e == cudaSuccess) cur = smem;
+  return e;
+}
+
 int check_device(const pccp_model* m) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return PCCP_ERR_CUDA;
@@ -1011,8 +1029,7 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
                    : k_propagate<512, 3, false, false, false>)
           : (track ? k_propagate<1024, 1, true, false, false>
                    : k_propagate<1024, 1, false, false, false>);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem)) != cudaSuccess) {
+  if (allow_smem(reinterpret_cast<const void*>(kern), smem) != cudaSuccess) {
     (void)cudaGetLastError();
     return PCCP_ERR_CUDA;
   }
@@ -1291,8 +1308,7 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
   if (smem > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   if (global && opts->threads <= 0) threads = 1024;
   const auto ksolve = solve_kernel(opts, global, stages > 0);
-  PCCP_CUDA(cudaFuncSetAttribute(ksolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem)));
+  PCCP_CUDA(allow_smem(reinterpret_cast<const void*>(ksolve), smem));
   int per_sm = 0;
   PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksolve, threads, smem));
   if (per_sm < 1) return PCCP_ERR_SMEM;
@@ -1445,10 +1461,8 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     eps_kernels<true, false>(learned, use_skip_stable(o->skip_stable, true), &kexp, &ksol);
   else
     eps_kernels<false, false>(learned, use_skip_stable(o->skip_stable, false), &kexp, &ksol);
-  PCCP_CUDA(cudaFuncSetAttribute(kexp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem)));
-  PCCP_CUDA(cudaFuncSetAttribute(ksol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem)));
+  PCCP_CUDA(allow_smem(reinterpret_cast<const void*>(kexp), smem));
+  PCCP_CUDA(allow_smem(reinterpret_cast<const void*>(ksol), smem));
   int occ_e = 0, occ_s = 0;
   PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_e, kexp, teams * team, smem));
   PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, ksol, teams * team, smem));

@@ -287,3 +287,58 @@ def test_host_default_chunking_large_batch():
     x, f = compare_batch(rcpsp_model(inst), lb, ub, st.numpy(), hlb.numpy(), hub.numpy(),
                          rows=sample)
     assert x + f == len(sample)
+
+
+def test_models_of_different_sizes_interleaved_and_threaded():
+    """A small model planned between two calls on a larger one (same kernel,
+    less shared memory) leaves the larger one launchable, in sequence and
+    from concurrent host threads on separate streams; results stay exact."""
+    import threading
+    big_inst, small_inst = config_instance("j30", 1), config_instance("tiny8", 3)
+    big, small = pccp.Model.from_rcpsp(big_inst), pccp.Model.from_rcpsp(small_inst)
+    assert big.info.table_bytes > 4 * small.info.table_bytes
+
+    def batch(inst, n, seed):
+        rows = pccp.rcpsp.build_rows(inst)
+        return pccp.rcpsp.node_stores(rows, draw_partial_assignments(inst.n, inst.horizon, n,
+                                                                     seed=seed))
+
+    blb, bub = batch(big_inst, 300, 2)
+    slb, sub = batch(small_inst, 300, 3)
+    ref_big, ref_small = run(big, blb, bub), run(small, slb, sub)
+
+    def same(ref, st, lb, ub):
+        fx = ref[0] == 0
+        return (np.array_equal(ref[0], st) and np.array_equal(ref[1][fx], lb[fx])
+                and np.array_equal(ref[2][fx], ub[fx]))
+
+    for _ in range(2):  # host entry point keeps its plan across the small model's calls
+        h = [torch.from_numpy(blb.copy()).pin_memory(), torch.from_numpy(bub.copy()).pin_memory()]
+        st, _ = pccp.propagate_host(big, h[0], h[1])
+        assert same(ref_big, st.numpy(), h[0].numpy(), h[1].numpy())
+        assert same(ref_small, *run(small, slb, sub)[:3])
+
+    errors = []
+
+    def worker(model, lb, ub, ref):
+        try:
+            stream = torch.cuda.Stream()
+            for _ in range(20):
+                with torch.cuda.stream(stream):
+                    dlb = torch.from_numpy(lb).cuda()
+                    dub = torch.from_numpy(ub).cuda()
+                    st, _ = pccp.propagate(model, dlb, dub, stream=stream)
+                stream.synchronize()
+                if not same(ref, st.cpu().numpy(), dlb.cpu().numpy(), dub.cpu().numpy()):
+                    errors.append("mismatch")
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append(repr(e))
+
+    ts = [threading.Thread(target=worker, args=a) for a in
+          ((big, blb, bub, ref_big), (small, slb, sub, ref_small),
+           (big, blb, bub, ref_big), (small, slb, sub, ref_small))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors[:3]
