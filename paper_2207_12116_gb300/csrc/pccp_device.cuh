@@ -323,6 +323,7 @@ struct Sweep {
   const uint32_t* prev_chg;
   const uint32_t* prev_dl;
   bool full;
+  int* grab;  // this sweep's claim counter (tables in global memory)
 };
 
 template <bool kTrack>
@@ -671,13 +672,25 @@ __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags
       const int4 h = tb.lin[r];
       eval_linear_thread_at<kTrack>(w, h, tb.terms + h.y, f);
     }
-    for (int r = tm.warp; r < tb.n_lin_long; r += tm.nwarps) {
-      if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
-      const int4 h = tb.lin_long[r];
-      eval_linear_warp_at<kTrack>(w, h, tb.terms_long + h.y, tm.lane, f);
+    // long rows, then blocks of 32 reified pairs, claimed by whole warps from
+    // the sweep's counter: rows of uneven cost (lengths, skipped rows, L2
+    // latency) leave no warp waiting at the barrier while others still work
+    const int n_blocks = (tb.n_rfp + 31) >> 5;
+    for (;;) {
+      int q = 0;
+      if (tm.lane == 0) q = atomicAdd(w.grab, 1);
+      q = __shfl_sync(0xffffffffu, q, 0);
+      if (q < tb.n_lin_long) {
+        if (skip_linear_long<kTrack>(w, q, tm.lane, f)) continue;
+        const int4 h = tb.lin_long[q];
+        eval_linear_warp_at<kTrack>(w, h, tb.terms_long + h.y, tm.lane, f);
+      } else if (q < tb.n_lin_long + n_blocks) {
+        const int r = ((q - tb.n_lin_long) << 5) + tm.lane;
+        if (r < tb.n_rfp) eval_reified_pair<kTrack, kQuiet>(w, tb.rfp[r], f);
+      } else {
+        break;
+      }
     }
-    for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr)
-      eval_reified_pair<kTrack, kQuiet>(w, tb.rfp[r], f);
     for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack, kQuiet>(w, tb.rf[r], f);
     for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
   } else {  // tables in shared memory: reified, temporal, linear
@@ -891,6 +904,8 @@ struct FixCtrl {
   int evals;
   int bytes;
   int pad;
+  int grab[2];  // claim counters of the sweeps over a table in global memory
+  int pad2[2];
 };
 
 // Work of `it` full sweeps (every row runs in each, so the count is exact);
@@ -930,13 +945,25 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
                                              const Track& tk, bool full, int max_iter,
                                              int& iters, Streamer* sm = nullptr) {
   int it = 0;
+  constexpr bool kClaim = kGlobal && !kStream;  // sweep_rows claims rows dynamically
+  if (kClaim) {  // counter of the first sweep; the barrier publishes it
+    if (tm.tid == 0) {
+      fc->grab[0] = 0;
+      fc->grab[1] = 0;
+    }
+    team_bar(tm.bar, tm.nthr);
+  }
   for (;;) {
     const int cur = it % 3, prv = (it + 2) % 3, nxt = (it + 1) % 3;
     if (kTrack) {
       for (int i = tm.tid; i < tk.W; i += tm.nthr) tk.chg[nxt * tk.W + i] = 0u;
       for (int i = tm.tid; i < tk.WL; i += tm.nthr) tk.dl[nxt * tk.WL + i] = 0u;
     }
-    const Sweep w{tb, st, tk, cur, tk.chg + prv * tk.W, tk.dl + prv * tk.WL, full || !kTrack};
+    // the next sweep's counter was last used by the previous sweep, which
+    // every warp left before the last barrier; this sweep's barrier publishes it
+    if (kClaim && tm.tid == 0) fc->grab[(it + 1) & 1] = 0;
+    const Sweep w{tb, st,   tk,   cur, tk.chg + prv * tk.W, tk.dl + prv * tk.WL, full || !kTrack,
+                  kClaim ? &fc->grab[it & 1] : nullptr};
     Flags f{false, false, 0, 0};
     if (kStream)
       sweep_rows_streamed<kTrack>(w, tm, f, *sm);
