@@ -658,7 +658,8 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
 // One full evaluation of every row of the table (one iteration of the
 // eventless loop).  Rows of one kind run back to back so warps stay uniform:
 // a thread per reified, temporal and short linear row, a warp per long
-// linear row.  Kind order (it never changes the fixed point, Sec. 3): with
+// linear row; dealt statically, except that with the table in global memory
+// warps claim the long rows and the reified pairs (w.grab).  Kind order (it never changes the fixed point, Sec. 3): with
 // the table in shared memory reified, temporal, linear; in global memory
 // linear, reified, temporal -- each the faster of the six orders measured
 // there (the second saves iterations on 120-task models, the first is
