@@ -8,7 +8,7 @@ only go from a lower to a higher task index, so the DAG is acyclic.
 The distributions mirror the shape of PSPLIB j30 (30 tasks, 4 resources), the
 data set the paper evaluates on; that data set itself is not reproduced.
 """
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import List, Tuple
 
 from .rng import SplitMix64

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle.rcpsp import rcpsp_model, node_store
+from oracle.rcpsp import rcpsp_model
 import paper_2207_12116_gb300 as pccp
 from paper_2207_12116_gb300 import autotune
 from synthetic import config_instance, draw_partial_assignments

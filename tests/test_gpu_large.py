@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from oracle import brute
-from oracle.rcpsp import rcpsp_model, node_store
+from oracle.rcpsp import rcpsp_model
 import paper_2207_12116_gb300 as pccp
 from synthetic import config_instance, draw_partial_assignments
 from tests.gpu_util import compare_batch

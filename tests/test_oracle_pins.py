@@ -2,7 +2,6 @@
 itself (brute-force enumeration, a closed form, the paper's theorems as
 executable invariants), chosen so a dropped term, a wrong sign, an off-by-one
 or a swapped operand in any guarded command fails at least one test."""
-import itertools
 
 import numpy as np
 import pytest
@@ -11,7 +10,7 @@ import oracle
 from oracle import brute
 from oracle.rcpsp import rcpsp_model, node_store, var_M
 from synthetic import SplitMix64, config_instance, draw_generic_model, draw_generic_store
-from synthetic.rcpsp import RcpspInstance, RcpspDistribution, draw_rcpsp
+from synthetic.rcpsp import RcpspDistribution, draw_rcpsp
 
 
 def hull(solutions, nv):
