@@ -87,6 +87,8 @@ def _load():
             lib.om_command.restype = ctypes.c_int
             lib.om_solve.argtypes = [P, P, P, P]
             lib.om_solve.restype = ctypes.c_int
+            lib.om_solve_traced.argtypes = [P, P, P, P, P, ctypes.c_int64, P]
+            lib.om_solve_traced.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -199,21 +201,41 @@ def command(model: Model, lb, ub, g: int):
     return kind, var.value, val.value
 
 
+NODE_FAILED, NODE_SOLUTION, NODE_BRANCH = 0, 1, 2
+TRACE_FIELDS = 6
+
+
 def solve(model: Model, mode: int = OPTIMISE, strategy: int = INPUT_ORDER,
-          node_limit: int = 0, obj_ub: int = INT64_MAX):
+          node_limit: int = 0, obj_ub: int = INT64_MAX, trace_cap: int = 0):
     """Depth-first branch and bound.  Returns a dict with status, objective,
-    witness (lb of the recorded solution), nodes, fails, solutions, sweeps."""
+    witness (lb of the recorded solution), nodes, fails, solutions, sweeps.
+    With trace_cap > 0 it also returns "trace": the first trace_cap nodes in
+    depth-first preorder, each (depth, decision var, side, value, outcome,
+    chosen var): the decision that created the node (var -1 for the root;
+    side 0 = left, ub <= value; 1 = right, lb >= value), the node's outcome
+    (NODE_FAILED / NODE_SOLUTION / NODE_BRANCH) and the variable it
+    branches on (-1 unless it branches)."""
     lib = _load()
     o = _SolveOpts(mode, strategy, node_limit, obj_ub)
     r = _SolveResult()
     w = np.zeros(max(model.n_vars, 1), dtype=np.int64)
-    rc = lib.om_solve(model.cptr, ctypes.addressof(o), ctypes.addressof(r), w.ctypes.data)
+    tr = np.zeros((max(trace_cap, 1), TRACE_FIELDS), dtype=np.int64)
+    tn = ctypes.c_int64(0)
+    if trace_cap > 0:
+        rc = lib.om_solve_traced(model.cptr, ctypes.addressof(o), ctypes.addressof(r),
+                                 w.ctypes.data, tr.ctypes.data, trace_cap, ctypes.addressof(tn))
+    else:
+        rc = lib.om_solve(model.cptr, ctypes.addressof(o), ctypes.addressof(r), w.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"oracle search aborted (code {rc})")
-    return {
+    out = {
         "status": r.status, "has_solution": bool(r.has_solution),
         "objective": int(r.objective) if r.has_solution else None,
         "witness": w[: model.n_vars].copy() if r.has_solution else None,
         "nodes": int(r.nodes), "fails": int(r.fails), "solutions": int(r.solutions),
         "sweeps": int(r.sweeps), "max_depth": int(r.max_depth),
     }
+    if trace_cap > 0:
+        out["trace"] = [tuple(int(x) for x in row) for row in tr[: min(tn.value, trace_cap)]]
+        out["trace_nodes"] = int(tn.value)
+    return out

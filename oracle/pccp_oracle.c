@@ -333,7 +333,33 @@ typedef struct {
   i64* ub;
   int32_t cap;
   int64_t sweep_cap;
+  /* optional record of every node in depth-first preorder (NULL: none) */
+  int64_t* trace;
+  int64_t trace_cap;
+  int64_t trace_n;
 } om_search;
+
+/* Outcome of a node in the search trace. */
+enum { OM_NODE_FAILED = 0, OM_NODE_SOLUTION = 1, OM_NODE_BRANCH = 2 };
+#define OM_TRACE_FIELDS 6
+
+/* Append one node to the trace: its depth, the decision that created it
+ * (variable, side 0 = left ub <= value / 1 = right lb >= value, value; the
+ * root has variable -1), its outcome and, for a branching node, the
+ * variable chosen (else -1). */
+static void trace_node(om_search* s, int32_t depth, int outcome, int32_t chosen) {
+  if (!s->trace) return;
+  if (s->trace_n < s->trace_cap) {
+    int64_t* t = s->trace + OM_TRACE_FIELDS * s->trace_n;
+    t[0] = depth;
+    t[1] = depth > 0 ? s->dvar[depth - 1] : -1;
+    t[2] = depth > 0 ? (s->dkind[depth - 1] == OM_TELL_UB ? 0 : 1) : -1;
+    t[3] = depth > 0 ? s->dval[depth - 1] : 0;
+    t[4] = outcome;
+    t[5] = chosen;
+  }
+  s->trace_n += 1;
+}
 
 /* Branching variable (index into the store) or -1 if all branch vars fixed. */
 static int32_t select_var(const om_model* m, int strategy, const i64* lb, const i64* ub) {
@@ -370,8 +396,13 @@ static void dfs(om_search* s, int32_t depth) {
   int st = om_propagate(m, s->lb, s->ub, OM_FORWARD, 0, s->sweep_cap, &sw);
   s->r->sweeps += sw;
   if (st == OM_NONTERMINATING) { s->stop = 4; return; }
-  if (st != OM_FIXPOINT) { s->r->fails += 1; return; }
+  if (st != OM_FIXPOINT) {
+    s->r->fails += 1;
+    trace_node(s, depth, OM_NODE_FAILED, -1);
+    return;
+  }
   int32_t v = select_var(m, s->o->strategy, s->lb, s->ub);
+  trace_node(s, depth, v < 0 ? OM_NODE_SOLUTION : OM_NODE_BRANCH, v);
   if (v < 0) {
     s->r->solutions += 1;
     i64 obj = (m->objective >= 0) ? s->lb[m->objective] : 0;
@@ -399,11 +430,16 @@ static void dfs(om_search* s, int32_t depth) {
 
 /* Returns 0 on success, -1 if the decision stack capacity was exceeded, -2 if
  * a propagation ran past its sweep bound (cannot happen for a correct
- * oracle; it turns a broken build into an error instead of a hang). */
-int om_solve(const om_model* m, const om_solve_opts* o, om_solve_result* r, i64* witness) {
+ * oracle; it turns a broken build into an error instead of a hang).
+ * trace (may be NULL): room for trace_cap nodes of OM_TRACE_FIELDS int64
+ * each (trace_node), filled in depth-first preorder; *trace_n (if not NULL)
+ * receives the number of nodes, which may exceed trace_cap. */
+int om_solve_traced(const om_model* m, const om_solve_opts* o, om_solve_result* r, i64* witness,
+                    int64_t* trace, int64_t trace_cap, int64_t* trace_n) {
   om_search s;
   memset(r, 0, sizeof(*r));
   s.m = m; s.o = o; s.r = r; s.witness = witness; s.best = 0; s.stop = 0;
+  s.trace = trace; s.trace_cap = trace ? trace_cap : 0; s.trace_n = 0;
   /* each decision strictly narrows one branch variable's interval; 64 per
    * variable bounds the depth for any int64 interval */
   s.cap = 64 * (m->n_branch > 0 ? m->n_branch : 1) + 1;
@@ -421,7 +457,12 @@ int om_solve(const om_model* m, const om_solve_opts* o, om_solve_result* r, i64*
   else r->status = r->has_solution ? OM_RES_OPTIMAL : OM_RES_INFEASIBLE;
   if (!r->has_solution) r->objective = 0;
   free(s.dvar); free(s.dkind); free(s.dval); free(s.lb); free(s.ub);
+  if (trace_n) *trace_n = s.trace_n;
   return rc;
+}
+
+int om_solve(const om_model* m, const om_solve_opts* o, om_solve_result* r, i64* witness) {
+  return om_solve_traced(m, o, r, witness, NULL, 0, NULL);
 }
 
 /* Batch driver: propagate n stores (row-major [n][n_vars]) one after another

@@ -1,6 +1,7 @@
 """Planted mistakes: each mutant is a copy of the oracle with one plausible
-error (a wrong sign, an off-by-one, a dropped or extra term).  The pins in
-test_oracle_pins.py must fail on every one of them.  Mutants are built and
+error (a wrong sign, an off-by-one, a dropped or extra term, another search
+order).  The pins in test_oracle_pins.py and test_oracle_search_pins.py must
+fail on every one of them.  Mutants are built and
 run on the CPU only."""
 import os
 import subprocess
@@ -33,7 +34,25 @@ MUTANTS = {
                                          "}\n      }\n    }\n    if (!changed)"),
     "solve_records_nonimproving": ("if (s->o->mode == OM_OPTIMISE) record = 1;",
                                    "if (s->o->mode == OM_OPTIMISE) record = (s->r->solutions == 1);"),
+    # search order: tie-break, split point, child order
+    "first_fail_ties_to_higher_index": ("if (best < 0 || w < best_w)", "if (best < 0 || w <= best_w)"),
+    "split_at_one_third": ("i64 mid = l + (u - l) / 2;", "i64 mid = l + (u - l) / 3;"),
+    "split_left_takes_smaller_half": ("i64 mid = l + (u - l) / 2;", "i64 mid = l + (u - l - 1) / 2;"),
+    "split_drops_lower_bound": ("i64 mid = l + (u - l) / 2;", "i64 mid = (u - l) / 2 > l ? (u - l) / 2 : l;"),
+    "right_child_first": (
+        """  s->dvar[depth] = v; s->dkind[depth] = OM_TELL_UB; s->dval[depth] = mid;
+  dfs(s, depth + 1);
+  if (s->stop) return;
+  s->dvar[depth] = v; s->dkind[depth] = OM_TELL_LB; s->dval[depth] = mid + 1;
+  dfs(s, depth + 1);""",
+        """  s->dvar[depth] = v; s->dkind[depth] = OM_TELL_LB; s->dval[depth] = mid + 1;
+  dfs(s, depth + 1);
+  if (s->stop) return;
+  s->dvar[depth] = v; s->dkind[depth] = OM_TELL_UB; s->dval[depth] = mid;
+  dfs(s, depth + 1);"""),
 }
+
+PIN_FILES = ("test_oracle_pins.py", "test_oracle_search_pins.py")
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -47,7 +66,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     c.write_text(mut)
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", str(c), "-o", str(so)])
     env = dict(os.environ, PCCP_ORACLE_LIB=str(so))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"]
+                       + [os.path.join(ROOT, "tests", f) for f in PIN_FILES],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
