@@ -545,6 +545,13 @@ def run_gpu(args):
             line["roofline"]["probes"] = probes
             meas = probes["smem_load"]["per_clk_per_sm"] * sms * (sm_mhz or 0) * 1e6 / 1e9
             line["roofline"]["frac_of_probe"] = achieved / meas if meas else None
+            # the second roof: the kernels' own access pattern, 8-byte interval
+            # loads at random indices (random banks halve the conflict-free rate)
+            gather = probes["smem_scattered_v2"]["per_clk_per_sm"] * sms * (sm_mhz or 0) * 1e6 / 1e9
+            line["roofline"]["gather_roof"] = {
+                "peak": gather, "unit": "GB/s", "frac": achieved / gather if gather else None,
+                "source": "measured: 8-byte shared loads at random indices "
+                          f"({probes['smem_scattered_v2']['per_clk_per_sm']:.1f} B/clk/SM)"}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(inst, nodes)
         if not args.no_search:

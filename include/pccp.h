@@ -313,9 +313,10 @@ void pccp_batch_destroy(pccp_batch* batch);
 
 /* No counterpart in the paper.  Same contract and results as
  * pccp_solve_batch, for callers that may not allocate device memory (hosts
- * that reserve all memory at start-up, plug-ins whose application owns the
- * allocator, work issued while a stream is being captured): this call makes no
- * cudaMalloc / cudaFree / memory-pool call of any kind.
+ * that reserve all memory at start-up and allocate nothing after a
+ * no-allocation point; plug-ins whose application owns the device allocator
+ * and forbids them to grow it): this call makes no cudaMalloc / cudaFree /
+ * memory-pool call of any kind.
  * Its scratch (model descriptors, results, witnesses, decision stacks, work
  * counter) is one fixed array of PCCP_NOALLOC_SCRATCH_BYTES in the library's
  * device memory; every GPU that loads the library holds it until the process
@@ -323,12 +324,16 @@ void pccp_batch_destroy(pccp_batch* batch);
  * anything is queued: descriptors 40 B + results 64 B per model, 4 B per
  * variable of every model, and at least one decision stack of
  * (32 x max branch variables + 2) x 8 B.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
- * on a device share the array, so calls that overlap on the GPU race:
- * serialise them (for instance on one stream).  results[i].elapsed_ms is the
- * host wall time of the whole call.  Errors: INVALID, SCRATCH, SMEM,
- * TIMEOUT, CUDA. */
+ * The first call on a device loads the library's device code there if it
+ * has not been loaded yet (CUDA loads modules lazily by default), which
+ * reserves the array, and looks up the array's address with that device
+ * current: make that first call before any no-allocation point.  The call
+ * copies through host memory and synchronises `stream` before it returns,
+ * so it must not be issued while `stream` is being captured into a graph
+ * (pccp_batch_solve_async is the capturable form).  All calls on a device
+ * share the array, so calls that overlap on the GPU race: serialise them
+ * (for instance on one stream).  results[i].elapsed_ms is the host wall time
+ * of the whole call.  Errors: INVALID, SCRATCH, SMEM, TIMEOUT, CUDA. */
 #define PCCP_NOALLOC_SCRATCH_BYTES (8u << 20)
 int pccp_solve_batch_noalloc(const pccp_model* const* models, int32_t n_models,
                              const pccp_solve_opts* opts, pccp_result* results, void* stream);

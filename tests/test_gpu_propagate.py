@@ -11,7 +11,7 @@ from oracle.rcpsp import rcpsp_model, node_store
 import paper_2207_12116_gb300 as pccp
 from synthetic import (config_instance, draw_generic_model, draw_generic_store,
                        draw_partial_assignments, SplitMix64)
-from tests.gpu_util import compare_batch, oracle_model_from_lists
+from tests.gpu_util import compare_batch, compare_whole_batch, oracle_model_from_lists
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -102,6 +102,44 @@ def test_j30_nodes_bit_exact():
     assert w[ok, 0].sum() < it2[ok].sum() * m.rows  # something was skipped
 
 
+def test_degenerate_temporal_rows_bit_exact():
+    """Rows the generic generator no longer draws (it keeps self-rows
+    x + d <= x at d <= 0 and backward rows mostly slack so that random
+    models keep solutions): a self-row with d > 0 (fails whatever the
+    store), precedence cycles of positive length (infeasible: bounds rise
+    until an interval empties) and of non-positive length (feasible), mixed
+    into generic models and compared with the oracle store by store."""
+    tot_f = tot_x = 0
+    for seed in range(40):
+        gm = draw_generic_model(4000 + seed)
+        g = SplitMix64.derive(seed, 77)
+        extra = []
+        kind = seed % 4
+        x, y, z = 0, 1 + g.uniform_int(0, 2), 4 + g.uniform_int(0, 1)
+        if kind == 0:
+            extra = [(x, x, 1 + g.uniform_int(0, 3))]
+        elif kind == 1:
+            extra = [(x, y, 2), (y, z, 1), (z, x, g.uniform_int(-2, 0))]
+        elif kind == 2:
+            extra = [(x, y, 3), (y, x, -3 - g.uniform_int(0, 2))]
+        else:
+            extra = [(x, x, -g.uniform_int(0, 3)), (y, z, -1), (z, y, 1)]
+        temporal = list(gm.temporal) + extra
+        m = pccp.Model.from_lists(gm.lb0, gm.ub0, temporal, gm.linear, gm.reified,
+                                  gm.objective, gm.branch)
+        om = oracle.Model(gm.lb0, gm.ub0, temporal, gm.linear, gm.reified, gm.objective,
+                          gm.branch)
+        lbs, ubs = zip(*[draw_generic_store(gm, 100 * seed + k) for k in range(16)])
+        lb, ub = np.array(lbs), np.array(ubs)
+        st, glb, gub, _ = run(m, lb, ub)
+        x_, f_ = compare_batch(om, lb, ub, st, glb, gub)
+        tot_x += x_
+        tot_f += f_
+        if kind in (0, 1):  # a positive self-row or a positive cycle: nothing survives
+            assert (st == pccp.PCCP_FAILED).all()
+    assert tot_f > 0 and tot_x > 0
+
+
 def test_uneven_models_bit_exact():
     for seed in range(6):
         inst = config_instance("mixed30_60", seed)
@@ -113,20 +151,20 @@ def test_uneven_models_bit_exact():
         compare_batch(om, lb, ub, st, glb, gub)
 
 
-def test_full_size_batch_sampled():
-    """The 10,000-node j30 batch in the default launch shape: a sample checked
-    store by store against the oracle, every store checked for properties
-    that hold at any size (re-propagating a fixed point changes nothing and
-    takes one iteration; results lie inside the input box)."""
+def test_full_size_batch_every_store():
+    """The 10,000-node j30 batch in the default launch shape: every store
+    compared with the oracle, element by element (the oracle's batch split
+    over the host cores), plus properties that hold at any size
+    (re-propagating a fixed point changes nothing and takes one iteration;
+    results lie inside the input box)."""
     inst = config_instance("j30", 0)
     m = pccp.Model.from_rcpsp(inst)
     om = rcpsp_model(inst)
     nodes = draw_partial_assignments(inst.n, inst.horizon, 10_000, seed=1)
     lb, ub = pccp.rcpsp.node_stores(pccp.rcpsp.build_rows(inst), nodes)
     st, glb, gub, it = run(m, lb, ub)
-    g = SplitMix64(2024)
-    sample = sorted({g.uniform_int(0, 9_999) for _ in range(300)} | {0, 9_999})
-    compare_batch(om, lb, ub, st, glb, gub, rows=sample)
+    nx, nf = compare_whole_batch(om, lb, ub, st, glb, gub)
+    assert nx + nf == 10_000 and nx > 0 and nf > 0
     ok = st == pccp.PCCP_FIXPOINT
     assert set(np.unique(st)) <= {0, 1}
     assert (glb[ok] >= lb[ok]).all() and (gub[ok] <= ub[ok]).all()
