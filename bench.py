@@ -285,12 +285,62 @@ EPS_TIME_MS = 2000
 EPS_NODE_LIMIT = 0  # > 0: the parallel runs stop on nodes instead of time
 
 
+COMPLETE_FAMILY, COMPLETE_MODELS = "mixed6_10", 256
+COMPLETE_BATCH = True
+
+
+def complete_batch_bench(pccp):
+    """Batched complete solves (the uneven-batch configuration): 256 seeded
+    6-10-task models, first-fail, each proved optimal by one team in the
+    sequential order, all in one persistent launch captured in a CUDA graph
+    and replayed, in the launch shape the autotuner picks (teams per CTA x
+    threads per team, timed on node-limited runs of the same batch).  The
+    device time of the replay is the time to the last proof; each model's
+    own time to proof comes from the kernel."""
+    import torch
+    from synthetic import config_instance
+    from paper_2207_12116_gb300 import autotune
+    models = [pccp.Model.from_rcpsp(config_instance(COMPLETE_FAMILY, s))
+              for s in range(COMPLETE_MODELS)]
+    t0 = time.perf_counter()
+    (teams, threads), report = autotune.tune_search_shape(models, node_limit=400)
+    tune_s = time.perf_counter() - t0
+    b = pccp.Batch(models, threads=threads, teams_per_cta=teams)
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph, stream=stream):
+            b.solve_async(strategy=pccp.PCCP_FIRST_FAIL, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    graph.replay()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    res = b.results(stream=stream)
+    nodes = sum(r["nodes"] for r in res)
+    per = sorted(r["model_ms"] for r in res)
+    return {"workload": f"{COMPLETE_MODELS} seeded models of {COMPLETE_FAMILY.replace('mixed', '')} "
+                        "tasks, 4 resources (config-2 distributions), first-fail, complete "
+                        "branch and bound, one team per model in the sequential order",
+            "complete": all(r["status"] == pccp.PCCP_RES_OPTIMAL for r in res), "graph": True,
+            "shape": {"teams_per_cta": teams, "threads": threads, "ctas": b.shape[2],
+                      "autotune_s": tune_s,
+                      "autotune_nodes_per_s": {f"{k[0]}x{k[1]}": v for k, v in report.items()}},
+            "ms_to_last_proof": ms, "nodes": nodes, "nodes_per_s": nodes / (ms / 1000),
+            "model_ms_to_proof": {"p50": per[len(per) // 2], "p99": per[int(0.99 * len(per)) - 1],
+                                  "max": per[-1], "sum": sum(per)},
+            "proven": sum(r["status"] == pccp.PCCP_RES_OPTIMAL for r in res),
+            "optima_sum": sum(r["objective"] for r in res)}
+
+
 def search_bench(pccp, cpu=True):
     """Search throughput: (a) one persistent launch solving 256 seeded
     30-60-task models depth first, one team per model, each stopped after
-    4,000 nodes; (b) every team of the GPU on one 30-task model (subproblems
-    from breadth-first growth, shared incumbent) for 2 s; (c) the oracle on a
-    bounded sample of (a)."""
+    4,000 nodes; (a') the batched complete solves of complete_batch_bench;
+    (b) every team of the GPU on one 30-task model (subproblems from
+    breadth-first growth, shared incumbent) for 2 s, and on one 120-task
+    model; (c) the oracle on a bounded sample of (a)."""
     from synthetic import config_instance
     insts = [config_instance("mixed30_60", s) for s in range(SEARCH_MODELS)]
     models = [pccp.Model.from_rcpsp(i) for i in insts]
@@ -306,6 +356,8 @@ def search_bench(pccp, cpu=True):
         "ms": ms, "nodes": nodes,
         "solutions_found": sum(r["solutions"] for r in res),
         "iterations_per_node": sum(r["iterations"] for r in res) / max(nodes, 1)}}
+    if COMPLETE_BATCH:
+        out["batched_complete"] = complete_batch_bench(pccp)
     for key, fam, what in (("parallel", "j30", "30-task"), ("parallel_large", "j120", "120-task")):
         m = pccp.Model.from_rcpsp(config_instance(fam, 0))
         if EPS_NODE_LIMIT:
@@ -567,8 +619,8 @@ def run_search_only(args):
     import torch
     import paper_2207_12116_gb300 as pccp
     torch.cuda.set_device(0)
-    global SEARCH_MODELS, SEARCH_NODE_LIMIT, EPS_NODE_LIMIT
-    SEARCH_MODELS, SEARCH_NODE_LIMIT, EPS_NODE_LIMIT = 64, 500, 2_000_000
+    global SEARCH_MODELS, SEARCH_NODE_LIMIT, EPS_NODE_LIMIT, COMPLETE_BATCH
+    SEARCH_MODELS, SEARCH_NODE_LIMIT, EPS_NODE_LIMIT, COMPLETE_BATCH = 64, 500, 2_000_000, False
     print(json.dumps(search_bench(pccp, cpu=False)), flush=True)
 
 

@@ -247,8 +247,22 @@ typedef struct {
   int32_t skip_stable;   /* as in pccp_launch_config (0: the library's choice); also
                             lets a left child run only the rows of the decided
                             variable first */
-  int32_t stream_table;  /* as in pccp_launch_config */
+  int32_t stream_table;  /* as in pccp_launch_config; batched searches stream only
+                            when some table does not fit one CTA beside its store
+                            (one team per CTA then) */
   const pccp_policy* policy; /* required with PCCP_LEARNED, created on this device */
+  int32_t teams_per_cta;    /* batched search: models searched side by side in one CTA,
+                               each by its own team in its own slot of shared memory
+                               (1..15; 0 = the library's choice) */
+  int32_t props_per_thread; /* propagator rows per thread per sweep: with threads == 0
+                               the team size is the largest model's rows divided by
+                               this, rounded up to whole warps (0 = not used) */
+  int32_t queue_granularity;/* parallel search: frontier subproblems per team before
+                               the persistent search starts (0 = 4) */
+  int32_t donate_nodes;     /* parallel search: after this many nodes in one
+                               subproblem a team hands its open right branches to the
+                               work queue while other teams wait for work
+                               (0 = the library's choice, < 0 = never) */
 } pccp_solve_opts;
 
 /* Counters and outcome of one search.  A node is every store propagated,
@@ -269,6 +283,9 @@ typedef struct {
   int64_t rows_evaluated;/* propagator rows evaluated (stable rows are skipped) */
   int32_t max_depth;
   float elapsed_ms;      /* device time of the search kernel */
+  float model_ms;        /* batched searches: device time of this model's own search,
+                            from its first node to its end (time to proof for a
+                            complete search); pccp_solve with deterministic = 0: 0 */
 } pccp_result;
 
 /* Solves one model.  Synchronous: returns after the result is filled.
@@ -278,9 +295,15 @@ int pccp_solve(const pccp_model* model, const pccp_solve_opts* opts, pccp_result
 
 /* Solves n_models models in one persistent launch; each model is searched by
  * one team in the deterministic order (opts->deterministic is ignored and
- * node_limit / time_limit_ms apply per model).  results[i] is filled for
- * models[i] (its witness pointer is honoured).  Synchronous.
- * Errors: INVALID, SMEM, TIMEOUT, CUDA. */
+ * node_limit / time_limit_ms apply per model), so every model's counts are
+ * those of pccp_solve with deterministic = 1.  A CTA holds teams_per_cta
+ * teams side by side, each in its own slot of shared memory; the models are
+ * queued largest table first and every team pulls the next one when it
+ * finishes.  A model's table prefix is staged in its team's slot when it
+ * fits beside the store, else read in place from global memory.
+ * results[i] is filled for models[i] (its witness pointer is honoured).
+ * Synchronous.  Errors: INVALID, SMEM (a store does not fit a slot),
+ * TIMEOUT, CUDA. */
 int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
                      const pccp_solve_opts* opts, pccp_result* results, void* stream);
 
@@ -289,12 +312,20 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
 /* A batch of models prepared once for repeated searches (the batched
  * configuration of the search: many models in one persistent launch).
  * pccp_batch_create allocates and uploads the model descriptors and the
- * result, witness and decision-stack buffers (synchronous); `threads` is the
- * team size per model (0 = 256; a multiple of 32, <= 1024).  The models must
- * outlive the batch.  Errors: INVALID, SMEM, CUDA. */
+ * result, witness and decision-stack buffers (synchronous).  The launch
+ * shape is fixed here: `threads` per team (0 = the library's choice; a
+ * multiple of 32) and `teams_per_cta` teams side by side per CTA (0 = the
+ * library's choice), as in pccp_solve_batch; later searches of the batch
+ * use it whatever their options say (stream_table is not used).  The models
+ * must outlive the batch.  Errors: INVALID, SMEM, CUDA. */
 typedef struct pccp_batch pccp_batch;
 int pccp_batch_create(const pccp_model* const* models, int32_t n_models, int32_t threads,
-                      pccp_batch** out);
+                      int32_t teams_per_cta, pccp_batch** out);
+
+/* The launch shape a batch was planned with (threads per team, teams per
+ * CTA, CTAs). */
+int pccp_batch_get_shape(const pccp_batch* batch, int32_t* threads, int32_t* teams_per_cta,
+                         int32_t* ctas);
 
 /* Queues one search of every model of the batch on `stream` (deterministic
  * order, one team per model; same semantics and results as
@@ -321,9 +352,9 @@ void pccp_batch_destroy(pccp_batch* batch);
  * counter) is one fixed array of PCCP_NOALLOC_SCRATCH_BYTES in the library's
  * device memory; every GPU that loads the library holds it until the process
  * exits.  A request whose scratch does not fit returns PCCP_ERR_SCRATCH before
- * anything is queued: descriptors 40 B + results 64 B per model, 4 B per
- * variable of every model, and at least one decision stack of
- * (32 x max branch variables + 2) x 8 B.
+ * anything is queued: descriptors 40 B + results 64 B per model and 4 B per
+ * variable of every model (plus, when tables are streamed, one decision
+ * stack of 8 B per possible decision for each team).
  * The first call on a device loads the library's device code there if it
  * has not been loaded yet (CUDA loads modules lazily by default), which
  * reserves the array, and looks up the array's address with that device

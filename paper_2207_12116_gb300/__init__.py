@@ -26,7 +26,7 @@ from . import rcpsp  # noqa: F401
 __all__ = ["Model", "pccp_model_create", "pccp_model_destroy", "pccp_model_get_info",
            "pccp_propagate", "pccp_propagate_ex", "pccp_solve", "pccp_solve_batch",
            "pccp_solve_batch_noalloc", "pccp_batch_create", "pccp_batch_solve_async",
-           "pccp_batch_results", "pccp_batch_destroy", "Batch", "Policy",
+           "pccp_batch_results", "pccp_batch_destroy", "pccp_batch_get_shape", "Batch", "Policy",
            "pccp_policy_create", "pccp_policy_destroy", "pccp_policy_get_weights",
            "pccp_policy_features", "pccp_policy_score", "pccp_policy_train_step",
            "pccp_error_string", "propagate", "propagate_host", "pccp_propagate_host", "solve",
@@ -91,12 +91,18 @@ def pccp_solve_batch_noalloc(handles, opts, results, stream):
     return load().pccp_solve_batch_noalloc(arr, n, ctypes.byref(opts), results, stream)
 
 
-def pccp_batch_create(handles, threads):
+def pccp_batch_create(handles, threads, teams_per_cta=0):
     n = len(handles)
     arr = (ctypes.c_void_p * n)(*[h.value for h in handles])
     h = ctypes.c_void_p()
-    rc = load().pccp_batch_create(arr, n, threads, ctypes.byref(h))
+    rc = load().pccp_batch_create(arr, n, threads, teams_per_cta, ctypes.byref(h))
     return rc, h
+
+
+def pccp_batch_get_shape(handle):
+    t, k, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    rc = load().pccp_batch_get_shape(handle, ctypes.byref(t), ctypes.byref(k), ctypes.byref(g))
+    return rc, (t.value, k.value, g.value)
 
 
 def pccp_batch_solve_async(handle, opts, stream):
@@ -296,11 +302,13 @@ def propagate_host(model: Model, lb, ub, status=None, iterations=None, chunk_sto
 
 
 def _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
-          skip_stable=None, policy=None, stream_table=False):
+          skip_stable=None, policy=None, stream_table=False, teams_per_cta=0,
+          props_per_thread=0, queue_granularity=0, donate_nodes=0):
     return _abi.pccp_solve_opts(strategy, mode, int(bool(deterministic)), obj_ub, node_limit,
                                 time_limit_ms, threads, blocks, _skip(skip_stable),
                                 int(bool(stream_table)),
-                                policy.handle if policy is not None else None)
+                                policy.handle if policy is not None else None,
+                                teams_per_cta, props_per_thread, queue_granularity, donate_nodes)
 
 
 def _result_dict(r, w):
@@ -309,14 +317,17 @@ def _result_dict(r, w):
             "witness": w.copy() if r.has_solution else None,
             "nodes": int(r.nodes), "fails": int(r.fails), "solutions": int(r.solutions),
             "iterations": int(r.iterations), "rows_evaluated": int(r.rows_evaluated),
-            "max_depth": int(r.max_depth), "elapsed_ms": float(r.elapsed_ms)}
+            "max_depth": int(r.max_depth), "elapsed_ms": float(r.elapsed_ms),
+            "model_ms": float(r.model_ms)}
 
 
 def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, deterministic=True,
           obj_ub=INT32_MAX, node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None,
-          skip_stable=None, policy=None, stream_table=False):
+          skip_stable=None, policy=None, stream_table=False, props_per_thread=0,
+          queue_granularity=0, donate_nodes=0):
     o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
-              skip_stable, policy, stream_table)
+              skip_stable, policy, stream_table, 0, props_per_thread, queue_granularity,
+              donate_nodes)
     w = np.zeros(model.n_vars, dtype=np.int32)
     r = _abi.pccp_result()
     r.witness = w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
@@ -327,11 +338,12 @@ def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, determini
 
 def solve_batch(models, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
                 node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None, noalloc=False,
-                skip_stable=None, policy=None, stream_table=False):
+                skip_stable=None, policy=None, stream_table=False, teams_per_cta=0,
+                props_per_thread=0):
     """Solve many models in one launch.  noalloc=True uses the allocation-free
     entry point (fixed device scratch; see include/pccp.h)."""
     o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, threads, blocks,
-              skip_stable, policy, stream_table)
+              skip_stable, policy, stream_table, teams_per_cta, props_per_thread)
     n = len(models)
     ws = [np.zeros(m.n_vars, dtype=np.int32) for m in models]
     res = (_abi.pccp_result * n)()
@@ -347,12 +359,19 @@ class Batch:
     """Models prepared for repeated batched searches; solve_async() only
     queues work on the stream (capturable in a CUDA graph)."""
 
-    def __init__(self, models, threads=0):
+    def __init__(self, models, threads=0, teams_per_cta=0):
         self.models = list(models)  # keep the models alive
-        rc, h = pccp_batch_create([m.handle for m in self.models], threads)
+        rc, h = pccp_batch_create([m.handle for m in self.models], threads, teams_per_cta)
         check(rc, "pccp_batch_create")
         self.handle = h
         self._ws = [np.zeros(m.n_vars, dtype=np.int32) for m in self.models]
+
+    @property
+    def shape(self):
+        """(threads per team, teams per CTA, CTAs) of the planned launch."""
+        rc, shp = pccp_batch_get_shape(self.handle)
+        check(rc, "pccp_batch_get_shape")
+        return shp
 
     def solve_async(self, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
                     node_limit=0, time_limit_ms=0, stream=None, skip_stable=None, policy=None):

@@ -58,7 +58,9 @@ class pccp_launch_config(ctypes.Structure):
 class pccp_solve_opts(ctypes.Structure):
     _fields_ = [("strategy", I32), ("mode", I32), ("deterministic", I32), ("obj_ub", I32),
                 ("node_limit", I64), ("time_limit_ms", I64), ("threads", I32), ("blocks", I32),
-                ("skip_stable", I32), ("stream_table", I32), ("policy", P)]
+                ("skip_stable", I32), ("stream_table", I32), ("policy", P),
+                ("teams_per_cta", I32), ("props_per_thread", I32), ("queue_granularity", I32),
+                ("donate_nodes", I32)]
 
 
 class pccp_policy_weights(ctypes.Structure):
@@ -69,7 +71,8 @@ class pccp_result(ctypes.Structure):
     _fields_ = [("status", I32), ("has_solution", I32), ("objective", I32),
                 ("witness", ctypes.POINTER(I32)),
                 ("nodes", I64), ("fails", I64), ("solutions", I64), ("iterations", I64),
-                ("rows_evaluated", I64), ("max_depth", I32), ("elapsed_ms", ctypes.c_float)]
+                ("rows_evaluated", I64), ("max_depth", I32), ("elapsed_ms", ctypes.c_float),
+                ("model_ms", ctypes.c_float)]
 
 
 # name -> (restype, argtypes): every entry point declared in include/pccp.h
@@ -85,7 +88,9 @@ SIGNATURES = {
                                         ctypes.POINTER(pccp_result), P]),
     "pccp_solve_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(P), I32, ctypes.POINTER(pccp_solve_opts),
                                                 ctypes.POINTER(pccp_result), P]),
-    "pccp_batch_create": (ctypes.c_int, [ctypes.POINTER(P), I32, I32, ctypes.POINTER(P)]),
+    "pccp_batch_create": (ctypes.c_int, [ctypes.POINTER(P), I32, I32, I32, ctypes.POINTER(P)]),
+    "pccp_batch_get_shape": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                            ctypes.POINTER(I32)]),
     "pccp_batch_solve_async": (ctypes.c_int, [P, ctypes.POINTER(pccp_solve_opts), P]),
     "pccp_batch_results": (ctypes.c_int, [P, ctypes.POINTER(pccp_result), P]),
     "pccp_batch_destroy": (None, [P]),

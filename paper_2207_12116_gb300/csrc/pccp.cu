@@ -55,14 +55,15 @@ struct InstanceDesc {
   int32_t witness_off;
   int32_t n_branch;
   int32_t max_iter;
-  int32_t pad;
+  int32_t index;  // the model's position in the caller's list (its result slot)
 };
 
 struct InstanceResult {
   int32_t status, has_solution, objective, max_depth;
   int64_t nodes, fails, solutions, iterations;
   int64_t evals;
-  int32_t error, pad;
+  int32_t error;
+  int32_t us;  // device time of this model's search, microseconds
 };
 
 static_assert(sizeof(InstanceDesc) == 40, "descriptor size is part of the scratch accounting");
@@ -88,6 +89,13 @@ struct SolveArgs {
   int x_words;                // learned strategy: feature rows per team (words)
   int max_vars_smem;          // store slots reserved per CTA
   const PolicyDev* policy;
+  // k_solve_slots: teams per CTA, each in a slot of slot_bytes of shared
+  // memory: [mbarrier | SearchCtrl | change words | feature rows |
+  //          decision stack (max_depth entries) | store | image]
+  int team_size;
+  int teams;
+  uint32_t slot_bytes;
+  uint32_t off_track, off_x, off_stack, off_store;  // byte offsets inside a slot
 };
 
 // Broadcast slots of one team's search.  Each slot has one writer (thread 0)
@@ -103,6 +111,14 @@ struct SearchCtrl {
   int next;    // next model index (CTA loop)
   int cur_depth;  // P1: depth of the node (features of the learned strategy)
   int pad;
+  // thread 0's search state (shared memory, so that the other threads do
+  // not hold it in registers through the fixed point)
+  struct {
+    int64_t nodes, fails, sols, iters, evals;
+    uint64_t t0;
+    int depth, max_d, best, objective, error;
+    int has_sol, limited, satisfied;
+  } ds;
 };
 
 constexpr unsigned long long kNoVar = ~0ull;
@@ -120,11 +136,14 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
                          int max_iter, int32_t* witness, InstanceResult* out, uint32_t* X,
                          Streamer* stream) {
   const int nv = tb.n_vars;
-  const uint64_t t0 = globaltimer_ns();
-  // thread-0 state
-  int64_t nodes = 0, fails = 0, sols = 0, iters = 0, evals = 0;
-  int depth = 0, max_d = 0, best = 0, objective = 0, error = 0;
-  bool has_sol = false, limited = false, satisfied = false;
+  // thread 0's state (only thread 0 reads or writes it)
+  auto& S = sc->ds;
+  if (tm.tid == 0) {
+    S.t0 = globaltimer_ns();
+    S.nodes = S.fails = S.sols = S.iters = S.evals = 0;
+    S.depth = S.max_d = S.best = S.objective = S.error = 0;
+    S.has_sol = S.limited = S.satisfied = 0;
+  }
   unsigned par = 0;
   // team-uniform: the store is a fixed point strengthened by marked tells
   // (left descent) rather than a store built from the root
@@ -137,24 +156,24 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
     // P1: limits, objective bound, reset of per-node slots
     if (tm.tid == 0) {
       int stop = 0;
-      if (a.node_limit > 0 && nodes >= a.node_limit) stop = 1;
-      if (a.time_limit_ns > 0 && static_cast<int64_t>(globaltimer_ns() - t0) > a.time_limit_ns)
+      if (a.node_limit > 0 && S.nodes >= a.node_limit) stop = 1;
+      if (a.time_limit_ns > 0 && static_cast<int64_t>(globaltimer_ns() - S.t0) > a.time_limit_ns)
         stop = 1;
       if (!stop && tb.objective >= 0) {
         int bound = a.obj_ub;
-        if (a.mode == PCCP_OPTIMISE && has_sol) bound = min(bound, best - 1);
+        if (a.mode == PCCP_OPTIMISE && S.has_sol) bound = min(bound, S.best - 1);
         if (bound < INT_MAX) {
           const int old = atom_min_s32(&st[tb.objective].y, bound);
           if (kTrack && old > bound) mark_changed(tb, tk, 2, tb.objective);
         }
       }
-      limited = stop != 0;
+      S.limited = stop != 0;
       sc->stop = stop;
       sc->fc.fail = 0;
       sc->fc.evals = 0;
       sc->fc.bytes = 0;
       sc->sel[par] = kNoVar;
-      sc->cur_depth = depth;
+      sc->cur_depth = S.depth;
     }
     team_bar(tm.bar, tm.nthr);  // N1
     if (sc->stop) break;
@@ -163,21 +182,21 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
         team_fixpoint<kTrack, kGlobal, kStream>(tb, st, tm, &sc->fc, tk, !seeded, max_iter, it,
                                                 stream);
     if (tm.tid == 0) {
-      ++nodes;
-      iters += it;
-      evals += sc->fc.evals;
-      max_d = max(max_d, depth);
+      ++S.nodes;
+      S.iters += it;
+      S.evals += sc->fc.evals;
+      S.max_d = max(S.max_d, S.depth);
     }
     if (fst == kError) {
       if (tm.tid == 0) {
-        error = 1;
-        limited = true;
+        S.error = 1;
+        S.limited = true;
       }
       break;
     }
     bool backtrack = true;
     if (fst == kFailed) {
-      if (tm.tid == 0) ++fails;
+      if (tm.tid == 0) ++S.fails;
     } else {
       // A5: variable selection by a team-wide minimum over branch variables
       unsigned long long* sel = &sc->sel[par];
@@ -201,15 +220,15 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
       const unsigned long long key = *sel;
       if (key == kNoVar) {  // every branch variable fixed: a solution
         if (tm.tid == 0) {
-          ++sols;
+          ++S.sols;
           const int z = tb.objective >= 0 ? st[tb.objective].x : 0;
-          const bool record = (a.mode == PCCP_OPTIMISE) || !has_sol;
+          const bool record = (a.mode == PCCP_OPTIMISE) || !S.has_sol;
           if (record) {
-            best = z;
-            objective = z;
+            S.best = z;
+            S.objective = z;
           }
-          has_sol = true;
-          if (a.mode == PCCP_OPTIMISE && tb.objective < 0) satisfied = true;
+          S.has_sol = true;
+          if (a.mode == PCCP_OPTIMISE && tb.objective < 0) S.satisfied = true;
           sc->record = record;
         }
         team_bar(tm.bar, tm.nthr);  // N3
@@ -223,19 +242,19 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
           const int v = tb.branch[static_cast<int>(key & 0xffffffffull)];
           const int2 D = st[v];
           const int m = D.x + (D.y - D.x) / 2;
-          if (depth >= a.max_depth) {
-            error = 2;
+          if (S.depth >= a.max_depth) {
+            S.error = 2;
           } else {
-            stack[depth] = make_int2(v, m);  // left: ub(v) <= m
-            ++depth;
+            stack[S.depth] = make_int2(v, m);  // left: ub(v) <= m
+            ++S.depth;
             atom_min_s32(&st[v].y, m);  // m < ub(v): always a change
             if (kTrack) mark_changed(tb, tk, 2, v);
           }
-          sc->err = error != 0;
+          sc->err = S.error != 0;
         }
         team_bar(tm.bar, tm.nthr);  // NB: publishes the error decision
         if (sc->err) {
-          if (tm.tid == 0) limited = true;
+          if (tm.tid == 0) S.limited = true;
           break;
         }
         seeded = true;
@@ -244,14 +263,14 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
     par ^= 1u;
     if (backtrack) {
       if (tm.tid == 0) {
-        while (depth > 0 && (static_cast<uint32_t>(stack[depth - 1].x) & kRightBit)) --depth;
-        if (depth == 0 || satisfied) {
+        while (S.depth > 0 && (static_cast<uint32_t>(stack[S.depth - 1].x) & kRightBit)) --S.depth;
+        if (S.depth == 0 || S.satisfied) {
           sc->depth = -1;
         } else {
-          const int2 e = stack[depth - 1];  // flip to the right child: lb(v) >= m + 1
-          stack[depth - 1] = make_int2(static_cast<int>(static_cast<uint32_t>(e.x) | kRightBit),
+          const int2 e = stack[S.depth - 1];  // flip to the right child: lb(v) >= m + 1
+          stack[S.depth - 1] = make_int2(static_cast<int>(static_cast<uint32_t>(e.x) | kRightBit),
                                        e.y + 1);
-          sc->depth = depth;
+          sc->depth = S.depth;
         }
       }
       team_bar(tm.bar, tm.nthr);  // N4
@@ -272,16 +291,20 @@ __device__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st,
     }
   }
   if (tm.tid == 0) {
-    out->status = limited ? PCCP_RES_LIMIT : (has_sol ? PCCP_RES_OPTIMAL : PCCP_RES_INFEASIBLE);
-    out->has_solution = has_sol;
-    out->objective = has_sol ? objective : 0;
-    out->max_depth = max_d;
-    out->nodes = nodes;
-    out->fails = fails;
-    out->solutions = sols;
-    out->iterations = iters;
-    out->evals = evals;
-    out->error = error;
+    out->status = S.limited ? PCCP_RES_LIMIT : (S.has_sol ? PCCP_RES_OPTIMAL : PCCP_RES_INFEASIBLE);
+    out->has_solution = S.has_sol;
+    out->objective = S.has_sol ? S.objective : 0;
+    out->max_depth = S.max_d;
+    out->nodes = S.nodes;
+    out->fails = S.fails;
+    out->solutions = S.sols;
+    out->iterations = S.iters;
+    out->evals = S.evals;
+    out->error = S.error;
+    {
+      const uint64_t us = (globaltimer_ns() - S.t0) / 1000u;
+      out->us = us > 0x7fffffffull ? 0x7fffffff : static_cast<int32_t>(us);
+    }
   }
 }
 
@@ -322,8 +345,8 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
     if (!kGlobal) {
       if (!load_image(img, d.image, d.image_bytes, mbar, parity)) {
         if (threadIdx.x == 0) {
-          a.res[i].status = PCCP_RES_LIMIT;
-          a.res[i].error = 3;
+          a.res[d.index].status = PCCP_RES_LIMIT;
+          a.res[d.index].error = 3;
         }
         return;
       }
@@ -341,9 +364,101 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
     }
     team_dfs<kTrack, kLearned, kGlobal, kStream>(tb, d.root, st, tm, sc, tk, stack, a,
                                                  d.max_iter, a.witness + d.witness_off,
-                                                 &a.res[i], X, &stream);
+                                                 &a.res[d.index], X, &stream);
   }
   if (kStream && open) stream_close(stream);
+}
+
+// Copy a table image prefix into a team's shared memory by TMA bulk copies
+// issued by the team's thread 0; every thread of the team waits (bounded) for
+// completion on the team's mbarrier.  The team barrier at the start orders
+// the team's earlier generic reads of dst before the async-proxy writes.
+// Returns the same value on every thread of the team: false if the wait gave
+// up (the caller must then not read dst).
+__device__ __forceinline__ bool team_load_image(uint8_t* dst, const uint8_t* src, uint32_t bytes,
+                                                uint64_t* mbar, uint32_t parity, const Team& tm) {
+  team_bar(tm.bar, tm.nthr);
+  if (tm.tid == 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(mbar, bytes);
+    const uint32_t chunk = 32768;
+    for (uint32_t o = 0; o < bytes; o += chunk) {
+      const uint32_t n = (bytes - o < chunk) ? (bytes - o) : chunk;
+      bulk_copy_g2s(dst + o, src + o, n, mbar);
+    }
+  }
+  bool ok = mbar_wait_bounded(mbar, parity, 1 << 22);
+  if (!ok) ok = mbar_wait_bounded(mbar, parity, 1 << 22);  // drain before giving up
+  return !team_bar_or(tm.bar, tm.nthr, !ok);
+}
+
+// Batched depth-first search with several teams per CTA (a.teams slots of
+// a.team_size threads).  Each team pulls models from the global queue (the
+// host orders it largest table first) and searches each one alone in the
+// sequential order (team_dfs), so every model's node counts are those of
+// the one-team search.  A model whose table prefix fits in the slot beside
+// its store is staged there by TMA bulk copies; a larger one is read in
+// place from the device image (through L1 / L2), which is where its change
+// tracking pays (kTrackS / kTrackG: skip stable rows for tables in shared /
+// global memory).
+template <bool kTrackS, bool kTrackG, bool kLearned>
+__global__ void __launch_bounds__(1024) k_solve_slots(SolveArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int team_id = threadIdx.x / a.team_size;
+  uint8_t* slot = smem + static_cast<size_t>(team_id) * a.slot_bytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(slot);
+  SearchCtrl* sc = reinterpret_cast<SearchCtrl*>(slot + 16);
+  uint32_t* track_base = reinterpret_cast<uint32_t*>(slot + a.off_track);
+  uint32_t* X = reinterpret_cast<uint32_t*>(slot + a.off_x);
+  int2* st = reinterpret_cast<int2*>(slot + a.off_store);
+  Team tm;
+  tm.tid = threadIdx.x - team_id * a.team_size;
+  tm.nthr = a.team_size;
+  tm.bar = 1 + team_id;
+  tm.lane = threadIdx.x & 31;
+  tm.warp = tm.tid >> 5;
+  tm.nwarps = a.team_size >> 5;
+  if (tm.tid == 0) {
+    mbar_init(mbar, 1);
+    fence_mbarrier_init();
+  }
+  int2* stack = reinterpret_cast<int2*>(slot + a.off_stack);
+  uint32_t parity = 0;
+  for (;;) {
+    team_bar(tm.bar, tm.nthr);  // the previous model is done (first pass: mbarrier ready)
+    if (tm.tid == 0) sc->next = atomicAdd(a.counter, 1);
+    team_bar(tm.bar, tm.nthr);
+    const int q = sc->next;
+    if (q >= a.n_inst) break;
+    const InstanceDesc d = a.inst[q];
+    InstanceResult* out = &a.res[d.index];
+    const TableHeader* hg = reinterpret_cast<const TableHeader*>(d.image);
+    // the image prefix after the store, 128-byte aligned, when it fits
+    const uint32_t img_off =
+        (a.off_store + 8u * static_cast<uint32_t>(d.n_vars) + 127u) & ~127u;
+    const uint32_t copy = static_cast<uint32_t>(kTrackS ? __ldg(&hg->track_bytes)
+                                                        : __ldg(&hg->core_bytes));
+    if (img_off + copy <= a.slot_bytes) {
+      uint8_t* img = slot + img_off;
+      if (!team_load_image(img, d.image, copy, mbar, parity, tm)) {
+        if (tm.tid == 0) {
+          out->status = PCCP_RES_LIMIT;
+          out->error = 3;
+        }
+        return;  // this team stops; its mbarrier phase may still be pending
+      }
+      parity ^= 1u;
+      const Tab tb = make_tab(img);
+      const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
+      team_dfs<kTrackS, kLearned, false, false>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
+                                                a.witness + d.witness_off, out, X, nullptr);
+    } else {
+      const Tab tb = make_tab(d.image);
+      const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
+      team_dfs<kTrackG, kLearned, true, false>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
+                                               a.witness + d.witness_off, out, X, nullptr);
+    }
+  }
 }
 
 // -------------------------------------------------------------- host model
@@ -353,6 +468,7 @@ struct Packed {
   int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective;
   int32_t n_seg;
   int64_t bytes_per_sweep;
+  uint32_t core_bytes, track_bytes;  // image prefixes copied to shared memory
 };
 
 size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
@@ -372,9 +488,12 @@ struct pccp_model {
   int32_t n_vars, n_t, n_rf, n_lin, n_terms, n_branch, objective;
   int32_t n_seg;  // stream segments of the table
   int32_t reordered;  // 1: shared-memory stores use the library's variable order
-  uint32_t image_bytes;
+  uint32_t image_bytes;  // whole image (read in place from global memory)
+  uint32_t core_bytes;   // prefix copied to shared memory by kernels without change tracking
+  uint32_t track_bytes;  // prefix copied by kernels that skip stable rows
   int64_t bytes_per_sweep;
   int32_t max_iter;  // every changing iteration narrows some bound by >= 1
+  int32_t max_decisions;  // bound on a search path's length (decision stack entries)
   uint8_t* d_mem;    // image, then root int2[n_vars]
   int2* d_root;
   HostPipe* pipe = nullptr;  // pccp_propagate_host's streams and slots (lazy)
@@ -763,13 +882,15 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   off = align16(off + TERMS_LONG.size() * sizeof(uint32_t));
   h.off_branch = static_cast<int32_t>(off);
   off = align16(off + static_cast<size_t>(d->n_branch) * sizeof(int32_t));
+  h.off_bstat = static_cast<int32_t>(off);
+  off = align16(off + BST.size() * sizeof(BranchStatic));
+  h.core_bytes = static_cast<int32_t>(off);  // what the eventless kernels copy
   h.off_adj_off = static_cast<int32_t>(off);
   off = align16(off + ADJ_OFF.size() * sizeof(int32_t));
   h.off_adj = static_cast<int32_t>(off);
   h.n_adj = static_cast<int32_t>(ADJ.size());
   off = align16(off + ADJ.size() * sizeof(int32_t));
-  h.off_bstat = static_cast<int32_t>(off);
-  off = align16(off + BST.size() * sizeof(BranchStatic));
+  h.track_bytes = static_cast<int32_t>(off);  // ... and the kernels that skip stable rows
   // Stream segments: the row sections cut into byte ranges of whole rows of
   // at most kStreamChunk bytes, 16-byte aligned (a range may run into the
   // section's padding), in the order a sweep evaluates them.
@@ -856,6 +977,8 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   p->objective = h.objective;
   p->bytes_per_sweep = bytes_per_sweep;
   p->n_seg = h.n_seg;
+  p->core_bytes = static_cast<uint32_t>(h.core_bytes);
+  p->track_bytes = static_cast<uint32_t>(h.track_bytes);
   return PCCP_OK;
 }
 
@@ -905,18 +1028,22 @@ int policy_x_words(const pccp_solve_opts* o, int max_branch) {
 // (the change bitmaps cost more than the rows they save there).
 bool use_skip_stable(int32_t opt, bool global) { return opt > 0 || (opt == 0 && global); }
 
-// The k_solve instantiation for a search's options (global: the tables are
-// read from global memory; stream: streamed through shared memory).
+// The one-team kernel that streams the tables through shared memory (a
+// batched search that asks for streaming when some table does not fit).
 using SolveKernel = void (*)(SolveArgs);
-template <bool kGlobal, bool kStream>
-SolveKernel solve_kernel_t(const pccp_solve_opts* o) {
-  if (o->strategy == PCCP_LEARNED) return k_solve<false, true, kGlobal, kStream>;
-  return use_skip_stable(o->skip_stable, kGlobal) ? k_solve<true, false, kGlobal, kStream>
-                                                  : k_solve<false, false, kGlobal, kStream>;
+SolveKernel stream_kernel(const pccp_solve_opts* o) {
+  if (o->strategy == PCCP_LEARNED) return k_solve<false, true, true, true>;
+  return use_skip_stable(o->skip_stable, true) ? k_solve<true, false, true, true>
+                                               : k_solve<false, false, true, true>;
 }
-SolveKernel solve_kernel(const pccp_solve_opts* o, bool global, bool stream) {
-  if (stream) return solve_kernel_t<true, true>(o);
-  return global ? solve_kernel_t<true, false>(o) : solve_kernel_t<false, false>(o);
+
+// The k_solve_slots instantiation for a search's options: change tracking
+// for tables staged in shared memory / read from global memory.
+SolveKernel slots_kernel(const pccp_solve_opts* o) {
+  if (o->strategy == PCCP_LEARNED) return k_solve_slots<false, false, true>;
+  if (o->skip_stable > 0) return k_solve_slots<true, true, false>;
+  if (o->skip_stable < 0) return k_solve_slots<false, false, false>;
+  return k_solve_slots<false, true, false>;
 }
 
 // Strategy and policy checks shared by the search entry points.
@@ -984,6 +1111,7 @@ int check_device(const pccp_model* m) {
 struct PropPlan {
   void (*kern)(PropArgs);
   bool table_global;
+  uint32_t copy_bytes;  // image prefix staged in shared memory (0: read in place)
   int stages;  // stream buffers per team (0: rows read in place)
   int team, teams, grid, max_grid;
   size_t smem;
@@ -998,11 +1126,14 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   if (team % 32 != 0 || team > 1024) return PCCP_ERR_INVALID;
   const size_t per_team = sizeof(PropCtrl) + 4 * ((track_words(m->n_vars, m->n_lin) + 3) & ~3) +
                           static_cast<size_t>(m->n_vars) * sizeof(int2);
-  // the table lives in shared memory when it fits beside one team's store;
+  // the table lives in shared memory when it fits beside one team's store
+  // (the prefix the kernel needs: with change tracking, the adjacency too);
   // otherwise every CTA reads it from the device image (through L1 / L2)
-  const bool global = static_cast<size_t>(m->image_bytes) + 16 + per_team >
+  const uint32_t img_smem =
+      use_skip_stable(cfg ? cfg->skip_stable : 0, false) ? m->track_bytes : m->core_bytes;
+  const bool global = static_cast<size_t>(img_smem) + 16 + per_team >
                       static_cast<size_t>(smem_max);
-  const size_t base = (global ? 0 : static_cast<size_t>(m->image_bytes)) + 16;
+  const size_t base = (global ? 0 : static_cast<size_t>(img_smem)) + 16;
   if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   if (global && !(cfg && cfg->team_threads > 0)) team = 1024;
   int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
@@ -1044,6 +1175,7 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   const int want = (n_stores + teams - 1) / teams;
   p->kern = kern;
   p->table_global = global;
+  p->copy_bytes = global ? 0u : img_smem;
   p->stages = stages;
   p->team = team;
   p->teams = teams;
@@ -1067,7 +1199,7 @@ int launch_propagate(const pccp_model* m, const PropPlan& plan, int32_t n_stores
   a.status = status;
   a.iters = iterations;
   a.counter = counter;
-  a.image_bytes = m->image_bytes;
+  a.image_bytes = plan.table_global ? m->image_bytes : plan.copy_bytes;
   a.n_vars = m->n_vars;
   a.n_stores = n_stores;
   a.team_size = plan.team;
@@ -1081,6 +1213,207 @@ int launch_propagate(const pccp_model* m, const PropPlan& plan, int32_t n_stores
   const int grid = std::max(1, std::min((n_stores + plan.teams - 1) / plan.teams, plan.max_grid));
   plan.kern<<<grid, plan.team * plan.teams, plan.smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? PCCP_OK : PCCP_ERR_CUDA;
+}
+
+// Launch plan of a batched search (pccp_solve_batch, pccp_batch_*,
+// pccp_solve_batch_noalloc).
+struct BatchPlan {
+  SolveKernel kern;
+  bool slots;            // k_solve_slots; else the one-team streamed kernel
+  int team, teams, grid, max_depth;
+  size_t smem;           // dynamic shared memory per CTA
+  uint32_t slot_bytes, off_track, off_x, off_stack, off_store;
+  int xw, max_tw, max_vars, stages;
+};
+
+// Shared memory a model needs in a slot whose store starts at off_store:
+// the store, then its table prefix 128-byte aligned (when `staged`).
+uint32_t slot_need(const pccp_model* m, uint32_t off_store, bool track, bool staged) {
+  const uint32_t st_end = off_store + 8u * static_cast<uint32_t>(m->n_vars);
+  if (!staged) return st_end;
+  return ((st_end + 127u) & ~127u) + (track ? m->track_bytes : m->core_bytes);
+}
+
+// Plans a batched search.  any_strategy: room for the learned strategy's
+// feature rows and an occupancy valid for every strategy's kernel (a batch
+// planned once for later searches).  Returns SMEM when some store does not
+// fit a slot.
+int plan_batch(const pccp_model* const* models, int32_t n, const pccp_solve_opts* o,
+               bool any_strategy, BatchPlan* p) {
+  const int smem_max = max_dyn_smem();
+  const int sms = sm_count();
+  if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
+  int32_t max_vars = 0, max_branch = 0, max_tw = 0, max_seg = 0, max_rows = 0, max_dec = 2;
+  uint32_t max_core = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const pccp_model* m = models[i];
+    max_dec = std::max(max_dec, m->max_decisions);
+    max_vars = std::max(max_vars, m->n_vars);
+    max_branch = std::max(max_branch, m->n_branch);
+    max_tw = std::max(max_tw, track_words(m->n_vars, m->n_lin));
+    max_seg = std::max(max_seg, m->n_seg);
+    max_rows = std::max(max_rows, m->n_t + m->n_rf + m->n_lin);
+    max_core = std::max(max_core, m->core_bytes);
+  }
+  if (o->threads < 0 || o->threads % 32 != 0 || o->threads > 1024) return PCCP_ERR_INVALID;
+  if (o->teams_per_cta < 0 || o->teams_per_cta > kMaxTeamsPerCta) return PCCP_ERR_INVALID;
+  if (o->props_per_thread < 0) return PCCP_ERR_INVALID;
+  p->xw = any_strategy ? 8 * ((max_branch + 15) & ~15) : policy_x_words(o, max_branch);
+  p->max_tw = max_tw;
+  p->max_vars = max_vars;
+  p->max_depth = max_dec;
+  p->off_track = static_cast<uint32_t>(align16(16 + sizeof(SearchCtrl)));
+  p->off_x = p->off_track + 4u * static_cast<uint32_t>((max_tw + 3) & ~3);
+  p->off_stack = static_cast<uint32_t>(align16(p->off_x + 4u * static_cast<uint32_t>(p->xw)));
+  p->off_store = static_cast<uint32_t>(
+      align16(p->off_stack + sizeof(int2) * static_cast<size_t>(p->max_depth)));
+  const bool track_s = o->strategy != PCCP_LEARNED && o->skip_stable > 0;
+  // streaming (one team per CTA, the old kernel) only when asked for and some
+  // table prefix does not fit one CTA beside its store
+  bool all_fit_one = true;
+  for (int32_t i = 0; i < n; ++i)
+    all_fit_one = all_fit_one && slot_need(models[i], p->off_store, track_s, true) <=
+                                     static_cast<uint32_t>(smem_max);
+  if (o->stream_table > 0 && !all_fit_one && !any_strategy) {
+    bool global = false;
+    int stages = 0;
+    const size_t smem = plan_solve_smem(max_core, max_tw, max_vars, smem_max, &global, p->xw,
+                                        o->stream_table, max_seg, &stages);
+    if (global && stages > 0) {
+      if (smem > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
+      p->slots = false;
+      p->kern = stream_kernel(o);
+      p->team = o->threads > 0 ? o->threads : 1024;
+      p->teams = 1;
+      p->smem = smem;
+      p->stages = stages;
+      p->slot_bytes = p->off_track = p->off_x = p->off_stack = p->off_store = 0;
+      PCCP_CUDA(allow_smem(reinterpret_cast<const void*>(p->kern), smem));
+      int per_sm = 0;
+      PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kern, p->team, smem));
+      if (per_sm < 1) return PCCP_ERR_SMEM;
+      p->grid = std::max(1, std::min(n, sms * per_sm));
+      if (o->blocks > 0) p->grid = std::min(p->grid, static_cast<int>(o->blocks));
+      return PCCP_OK;
+    }
+  }
+  p->slots = true;
+  p->stages = 0;
+  p->kern = slots_kernel(o);
+  // teams per CTA: asked for, else the most slots (up to 8) in which every
+  // model's table fits beside its store, else one
+  int teams = o->teams_per_cta;
+  if (teams == 0) {
+    teams = 1;
+    const int k_max = std::min(8, 1024 / std::max(o->threads, 32));
+    for (int k = k_max; k >= 2; --k) {
+      const uint32_t room = static_cast<uint32_t>(smem_max / k) & ~127u;
+      bool fit = true;
+      for (int32_t i = 0; fit && i < n; ++i)
+        fit = slot_need(models[i], p->off_store, track_s, true) <= room;
+      if (fit) {
+        teams = k;
+        break;
+      }
+    }
+  }
+  int team = o->threads;
+  if (team == 0 && o->props_per_thread > 0)
+    team = std::min(1024 / teams, std::max(32, ((max_rows + o->props_per_thread - 1) /
+                                                    o->props_per_thread + 31) & ~31));
+  if (team == 0) team = all_fit_one ? std::min(256, (1024 / teams) & ~31) : (1024 / teams) & ~31;
+  if (team < 32 || team * teams > 1024) return PCCP_ERR_INVALID;
+  // slot size: what the largest model needs (staged when it fits), at most
+  // an equal share of the CTA's shared memory
+  const uint32_t room = static_cast<uint32_t>(smem_max / teams) & ~127u;
+  uint32_t want = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const uint32_t staged = slot_need(models[i], p->off_store, track_s, true);
+    const uint32_t need = staged <= room ? staged : slot_need(models[i], p->off_store, false, false);
+    want = std::max(want, need);
+  }
+  if (want > room) return PCCP_ERR_SMEM;  // a store alone does not fit
+  p->slot_bytes = (want + 127u) & ~127u;
+  p->team = team;
+  p->teams = teams;
+  p->smem = static_cast<size_t>(teams) * p->slot_bytes;
+  // (a fixed array: the allocation-free entry point plans with this too)
+  SolveKernel kerns[8] = {p->kern};
+  int n_kerns = 1;
+  if (any_strategy) {
+    pccp_solve_opts q = *o;
+    for (int strategy : {PCCP_INPUT_ORDER, PCCP_LEARNED})
+      for (int skip : {-1, 0, 1}) {
+        q.strategy = strategy;
+        q.skip_stable = skip;
+        if (n_kerns < 8) kerns[n_kerns++] = slots_kernel(&q);
+      }
+  }
+  int per_sm = 1 << 30;
+  for (int ki = 0; ki < n_kerns; ++ki) {
+    const SolveKernel k = kerns[ki];
+    PCCP_CUDA(allow_smem(reinterpret_cast<const void*>(k), p->smem));
+    int occ = 0;
+    PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, team * teams, p->smem));
+    per_sm = std::min(per_sm, occ);
+  }
+  if (per_sm < 1) return PCCP_ERR_SMEM;
+  p->grid = std::max(1, std::min((n + teams - 1) / teams, sms * per_sm));
+  if (o->blocks > 0) p->grid = std::min(p->grid, static_cast<int>(o->blocks));
+  return PCCP_OK;
+}
+
+// Queue order of a batch: largest table first (ties by position), so the
+// longest searches start first and the small ones fill the tail.
+std::vector<int32_t> batch_order(const pccp_model* const* models, int32_t n) {
+  std::vector<int32_t> ord(n);
+  for (int32_t i = 0; i < n; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [models](int32_t a, int32_t b) {
+    return models[a]->image_bytes > models[b]->image_bytes;
+  });
+  return ord;
+}
+
+// Descriptor of model i (position `index` in the caller's list).
+InstanceDesc instance_desc(const pccp_model* m, int32_t index, int32_t witness_off) {
+  InstanceDesc d;
+  d.image = m->d_mem;
+  d.root = m->d_root;
+  d.image_bytes = m->image_bytes;
+  d.n_vars = m->n_vars;
+  d.witness_off = witness_off;
+  d.n_branch = m->n_branch;
+  d.max_iter = m->max_iter;
+  d.index = index;
+  return d;
+}
+
+// Kernel arguments of a planned batched search (buffers filled by the caller).
+SolveArgs batch_args(const BatchPlan& p, const pccp_solve_opts* o, int32_t n) {
+  SolveArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n_inst = n;
+  a.max_depth = p.max_depth;
+  a.mode = o->mode;
+  a.strategy = o->strategy;
+  a.obj_ub = o->obj_ub;
+  a.node_limit = o->node_limit;
+  a.time_limit_ns = o->time_limit_ms > 0 ? o->time_limit_ms * 1000000ll : 0;
+  a.max_image_bytes = 0;  // the streamed kernel reads every table from global memory
+  a.max_track_words = p.max_tw;
+  a.table_global = 1;
+  a.stream_stages = p.stages;
+  a.x_words = p.xw;
+  a.max_vars_smem = p.max_vars;
+  a.policy = o->strategy == PCCP_LEARNED ? policy_dev(o->policy) : nullptr;
+  a.team_size = p.team;
+  a.teams = p.teams;
+  a.slot_bytes = p.slot_bytes;
+  a.off_track = p.off_track;
+  a.off_x = p.off_x;
+  a.off_stack = p.off_stack;
+  a.off_store = p.off_store;
+  return a;
 }
 
 }  // namespace
@@ -1170,6 +1503,8 @@ int pccp_model_create(const pccp_model_desc* desc_user, pccp_model** out) {
   m->n_branch = p.n_branch;
   m->objective = p.objective;
   m->image_bytes = static_cast<uint32_t>(p.image.size());
+  m->core_bytes = p.core_bytes;
+  m->track_bytes = p.track_bytes;
   m->bytes_per_sweep = p.bytes_per_sweep;
   m->n_seg = p.n_seg;
   m->reordered = 0;
@@ -1179,6 +1514,18 @@ int pccp_model_create(const pccp_model_desc* desc_user, pccp_model** out) {
     int64_t w = 3;
     for (int v = 0; v < p.n_vars; ++v) w += static_cast<int64_t>(desc->ub0[v]) - desc->lb0[v];
     m->max_iter = static_cast<int32_t>(std::min<int64_t>(w, kDefaultMaxIter));
+    // a split leaves at most floor(width / 2) on either side, so a branch
+    // variable of root width w takes at most bitlen(w) decisions on one path
+    int64_t dec = 2;
+    for (int32_t k = 0; k < p.n_branch; ++k) {
+      const int32_t v = desc->branch_vars[k];
+      uint32_t wv = static_cast<uint32_t>(static_cast<int64_t>(desc->ub0[v]) - desc->lb0[v]);
+      while (wv) {
+        ++dec;
+        wv >>= 1;
+      }
+    }
+    m->max_decisions = static_cast<int32_t>(std::min<int64_t>(dec, INT32_MAX));
   }
   // device memory: image | root int2[n] | internal_of int32[n] | user_of int32[n]
   const size_t root_off = align16(p.image.size());
@@ -1230,7 +1577,7 @@ int pccp_model_get_info(const pccp_model* m, pccp_model_info* info) {
   info->table_bytes = static_cast<int32_t>(m->image_bytes);
   info->bytes_per_sweep = m->bytes_per_sweep;
   const int smem_max = max_dyn_smem();
-  int64_t room = static_cast<int64_t>(smem_max) - m->image_bytes - 32;
+  int64_t room = static_cast<int64_t>(smem_max) - m->core_bytes - 32;
   info->max_store_vars = room > 0 ? static_cast<int32_t>(std::min<int64_t>(room / 8, 65535)) : 0;
   info->n_segments = m->n_seg;
   info->reordered = m->reordered;
@@ -1270,51 +1617,27 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     const int rc0 = check_strategy(opts);
     if (rc0 != PCCP_OK) return rc0;
   }
-  const int smem_max = max_dyn_smem();
-  const int sms = sm_count();
-  if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
-  int threads = opts->threads > 0 ? opts->threads : 256;
-  if (threads % 32 != 0 || threads > 1024) return PCCP_ERR_INVALID;
-
   std::vector<InstanceDesc> desc(n_models);
-  uint32_t max_img = 0;
-  int32_t max_vars = 0, max_branch = 0, max_tw = 0, max_seg = 0;
+  std::vector<int32_t> woff(n_models);
   int64_t wit_total = 0;
   for (int32_t i = 0; i < n_models; ++i) {
     const pccp_model* m = models[i];
     if (!m) return PCCP_ERR_INVALID;
     const int rc = check_device(m);
     if (rc != PCCP_OK) return rc;
-    desc[i].image = m->d_mem;
-    desc[i].root = m->d_root;
-    desc[i].image_bytes = m->image_bytes;
-    desc[i].n_vars = m->n_vars;
-    desc[i].n_branch = m->n_branch;
-    desc[i].witness_off = static_cast<int32_t>(wit_total);
-    desc[i].max_iter = m->max_iter;
+    woff[i] = static_cast<int32_t>(wit_total);
     wit_total += m->n_vars;
     if (wit_total > INT32_MAX) return PCCP_ERR_INVALID;
-    max_img = std::max(max_img, m->image_bytes);
-    max_vars = std::max(max_vars, m->n_vars);
-    max_branch = std::max(max_branch, m->n_branch);
-    max_tw = std::max(max_tw, track_words(m->n_vars, m->n_lin));
-    max_seg = std::max(max_seg, m->n_seg);
   }
-  bool global = false;
-  int stages = 0;
-  const int xw = policy_x_words(opts, max_branch);
-  const size_t smem = plan_solve_smem(max_img, max_tw, max_vars, smem_max, &global, xw,
-                                      opts->stream_table, max_seg, &stages);
-  if (smem > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
-  if (global && opts->threads <= 0) threads = 1024;
-  const auto ksolve = solve_kernel(opts, global, stages > 0);
-  PCCP_CUDA(allow_smem(reinterpret_cast<const void*>(ksolve), smem));
-  int per_sm = 0;
-  PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksolve, threads, smem));
-  if (per_sm < 1) return PCCP_ERR_SMEM;
-  int grid = std::min(n_models, sms * per_sm);
-  if (opts->blocks > 0) grid = std::min(grid, static_cast<int>(opts->blocks));
-  const int max_depth = 32 * std::max(max_branch, 1) + 2;
+  BatchPlan plan;
+  {
+    const int rc = plan_batch(models, n_models, opts, false, &plan);
+    if (rc != PCCP_OK) return rc;
+  }
+  const std::vector<int32_t> ord = batch_order(models, n_models);
+  for (int32_t q = 0; q < n_models; ++q)
+    desc[q] = instance_desc(models[ord[q]], ord[q], woff[ord[q]]);
+  const int n_teams = plan.grid * plan.teams;
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // one scratch allocation: descriptors | results | witnesses | stacks | counter
@@ -1322,8 +1645,10 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
   const size_t o_res = align16(o_desc + desc.size() * sizeof(InstanceDesc));
   const size_t o_wit = align16(o_res + static_cast<size_t>(n_models) * sizeof(InstanceResult));
   const size_t o_stk = align16(o_wit + static_cast<size_t>(wit_total) * sizeof(int32_t));
-  const size_t o_cnt =
-      align16(o_stk + static_cast<size_t>(grid) * max_depth * sizeof(int2));
+  // decision stacks in global memory only for the streamed one-team kernel
+  // (k_solve_slots keeps each team's stack in its slot)
+  const size_t stacks = plan.slots ? 0 : static_cast<size_t>(n_teams) * plan.max_depth;
+  const size_t o_cnt = align16(o_stk + stacks * sizeof(int2));
   const size_t total = o_cnt + 16;
   uint8_t* dmem = nullptr;
   PCCP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dmem), total, s));
@@ -1341,32 +1666,18 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
       rc = PCCP_ERR_CUDA;
       break;
     }
-    SolveArgs a;
+    SolveArgs a = batch_args(plan, opts, n_models);
     a.inst = reinterpret_cast<const InstanceDesc*>(dmem + o_desc);
     a.res = reinterpret_cast<InstanceResult*>(dmem + o_res);
     a.witness = reinterpret_cast<int32_t*>(dmem + o_wit);
     a.stacks = reinterpret_cast<int2*>(dmem + o_stk);
     a.counter = reinterpret_cast<int*>(dmem + o_cnt);
-    a.n_inst = n_models;
-    a.max_depth = max_depth;
-    a.mode = opts->mode;
-    a.strategy = opts->strategy;
-    a.obj_ub = opts->obj_ub;
-    a.node_limit = opts->node_limit;
-    a.time_limit_ns = opts->time_limit_ms > 0 ? opts->time_limit_ms * 1000000ll : 0;
-    a.max_image_bytes = global ? 0 : max_img;
-    a.max_track_words = max_tw;
-    a.table_global = global ? 1 : 0;
-    a.stream_stages = stages;
-    a.x_words = xw;
-    a.max_vars_smem = max_vars;
-    a.policy = opts->strategy == PCCP_LEARNED ? policy_dev(opts->policy) : nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
       rc = PCCP_ERR_CUDA;
       break;
     }
     cudaEventRecord(e0, s);
-    ksolve<<<grid, threads, smem, s>>>(a);
+    plan.kern<<<plan.grid, plan.team * plan.teams, plan.smem, s>>>(a);
     if (cudaGetLastError() != cudaSuccess) {
       rc = PCCP_ERR_CUDA;
       break;
@@ -1404,8 +1715,9 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
     o.rows_evaluated = r.evals;
     o.max_depth = r.max_depth;
     o.elapsed_ms = ms;
+    o.model_ms = r.us / 1000.f;
     if (o.witness && r.has_solution)
-      std::memcpy(o.witness, hwit.data() + desc[i].witness_off,
+      std::memcpy(o.witness, hwit.data() + woff[i],
                   static_cast<size_t>(m->n_vars) * sizeof(int32_t));
     if (r.error == 1 || r.error == 3) rc = PCCP_ERR_TIMEOUT;
     if (r.error == 2) rc = PCCP_ERR_INVALID;
@@ -1442,9 +1754,12 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   const size_t per_team = sizeof(EpsCtrl) + 4 * ((track_words(m->n_vars, m->n_lin) + 3) & ~3) +
                           static_cast<size_t>(m->n_vars) * sizeof(int2) +
                           4 * static_cast<size_t>(xw);
-  const bool global = static_cast<size_t>(m->image_bytes) + 16 + per_team >
+  const uint32_t img_smem =
+      (o->strategy != PCCP_LEARNED && use_skip_stable(o->skip_stable, false)) ? m->track_bytes
+                                                                              : m->core_bytes;
+  const bool global = static_cast<size_t>(img_smem) + 16 + per_team >
                       static_cast<size_t>(smem_max);
-  const size_t base = (global ? 0 : static_cast<size_t>(m->image_bytes)) + 16;
+  const size_t base = (global ? 0 : static_cast<size_t>(img_smem)) + 16;
   if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   if (global && o->threads <= 0) team = 1024;
   const int fit = static_cast<int>((static_cast<size_t>(smem_max) - base) / per_team);
@@ -1471,7 +1786,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   int grid = sms * per_sm;
   if (o->blocks > 0) grid = std::min(grid, static_cast<int>(o->blocks));
   const int n_teams = grid * teams;
-  const int max_depth = 32 * std::max(m->n_branch, 1) + 2;
+  const int max_depth = m->max_decisions;
   const int target = 4 * n_teams;
   constexpr int kMaxSeedLen = 48;
   const size_t cap = 2 * static_cast<size_t>(target);
@@ -1507,6 +1822,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     std::memset(&a, 0, sizeof(a));
     a.image = m->d_mem;
     a.root = m->d_root;
+    a.image_bytes = global ? m->image_bytes : img_smem;
     a.g = reinterpret_cast<EpsGlobal*>(d + o_g);
     a.team_best = reinterpret_cast<int*>(d + o_tb);
     a.team_has = reinterpret_cast<int*>(d + o_th);
@@ -1514,7 +1830,6 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     a.stacks = reinterpret_cast<int2*>(d + o_stk);
     a.in_counter = reinterpret_cast<int*>(d + o_cnt);
     a.out_count = reinterpret_cast<int*>(d + o_cnt + 4);
-    a.image_bytes = m->image_bytes;
     a.n_vars = m->n_vars;
     a.max_iter = m->max_iter;
     a.teams = teams;
@@ -1615,6 +1930,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     res->rows_evaluated = static_cast<int64_t>(hg.evals);
     res->max_depth = hg.max_depth;
     res->elapsed_ms = ms;
+    res->model_ms = 0.f;
     res->status = hg.limited ? PCCP_RES_LIMIT
                              : (res->has_solution ? PCCP_RES_OPTIMAL : PCCP_RES_INFEASIBLE);
     if (res->witness && winner >= 0) {
@@ -1654,6 +1970,7 @@ int pccp_solve(const pccp_model* m, const pccp_solve_opts* opts, pccp_result* re
   }
   pccp_solve_opts o = *opts;
   if (o.threads <= 0) o.threads = 512;
+  o.teams_per_cta = 1;  // one model: one team
   const pccp_model* one[1] = {m};
   return pccp_solve_batch(one, 1, &o, result, stream);
 }

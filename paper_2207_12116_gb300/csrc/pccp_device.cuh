@@ -29,7 +29,11 @@ struct TableHeader {
   int32_t rows_sweep;   // row evaluations in one full sweep (a reified pair counts 2)
   int32_t bytes_sweep;  // their algorithmic bytes
   int32_t off_seg, n_seg;  // stream segments (tables read from global memory)
-  int32_t pad[2];
+  // prefixes of the image that a kernel copies into shared memory: core_bytes
+  // (header, rows, branch variables, their static features) without change
+  // tracking, track_bytes (also the variable -> linear-row adjacency) with it;
+  // the stream segment list after them is only read from global memory
+  int32_t core_bytes, track_bytes;
 };
 static_assert(sizeof(TableHeader) == 112, "header must be 112 bytes");
 

@@ -53,6 +53,10 @@ CONFIGS = {
     "j30": RcpspDistribution(30, 30, 4, (1, 10), (0, 5), (5, 10), 0.1),
     # uneven batched solves: 30-60 tasks, same distributions
     "mixed30_60": RcpspDistribution(30, 60, 4, (1, 10), (0, 5), (5, 10), 0.1),
+    # uneven batched complete solves: 6-10 tasks, same distributions (the
+    # largest sizes whose first-fail proofs all end within a few hundred
+    # thousand nodes of the plain sequential search)
+    "mixed6_10": RcpspDistribution(6, 10, 4, (1, 10), (0, 5), (5, 10), 0.1),
     # learned-branching family: 60 tasks
     "j60": RcpspDistribution(60, 60, 4, (1, 10), (0, 5), (5, 10), 0.1),
     # large family: 120 tasks
