@@ -287,51 +287,86 @@ EPS_NODE_LIMIT = 0  # > 0: the parallel runs stop on nodes instead of time
 
 COMPLETE_FAMILY, COMPLETE_MODELS = "mixed6_10", 256
 COMPLETE_BATCH = True
+COMPLETE_SEQUENTIAL = True  # the one-team-per-model form too (about a minute)
+LEARNED_IN_BENCH = True     # train a policy (~20 s) and time the learned form
 
 
-def complete_batch_bench(pccp):
-    """Batched complete solves (the uneven-batch configuration): 256 seeded
-    6-10-task models, first-fail, each proved optimal by one team in the
-    sequential order, all in one persistent launch captured in a CUDA graph
-    and replayed, in the launch shape the autotuner picks (teams per CTA x
-    threads per team, timed on node-limited runs of the same batch).  The
-    device time of the replay is the time to the last proof; each model's
-    own time to proof comes from the kernel."""
+def _graph_solve(pccp, batch, **kw):
+    """One search of a reusable batch captured in a CUDA graph and replayed;
+    returns (device ms of the replay, results)."""
     import torch
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph, stream=stream):
+            batch.solve_async(stream=stream, **kw)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):  # replay on the stream the events are recorded on
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), batch.results(stream=stream)
+
+
+def _proof_summary(pccp, ms, res):
+    nodes = sum(r["nodes"] for r in res)
+    per = sorted(r["model_ms"] for r in res)
+    return {"ms_to_last_proof": ms, "nodes": nodes, "nodes_per_s": nodes / (ms / 1000),
+            "proven": sum(r["status"] == pccp.PCCP_RES_OPTIMAL for r in res),
+            "complete": all(r["status"] == pccp.PCCP_RES_OPTIMAL for r in res),
+            "model_ms_to_proof": {"p50": per[len(per) // 2], "p99": per[int(0.99 * len(per)) - 1],
+                                  "max": per[-1]}}
+
+
+def complete_batch_bench(pccp, policy=None, training=None):
+    """Batched complete solves (the uneven-batch configuration): 256 seeded
+    6-10-task models proved optimal, each search one CUDA graph replay of a
+    reusable batch in the launch shape the autotuner picks.  Two forms:
+    parallel (every team over one shared queue of subproblems of all models,
+    work donation, per-model incumbents) for the plain strategies and the
+    learned policy, and the sequential order (one team per model, node
+    counts equal to the oracle's) for first-fail."""
     from synthetic import config_instance
     from paper_2207_12116_gb300 import autotune
     models = [pccp.Model.from_rcpsp(config_instance(COMPLETE_FAMILY, s))
               for s in range(COMPLETE_MODELS)]
     t0 = time.perf_counter()
-    (teams, threads), report = autotune.tune_search_shape(models, node_limit=400)
+    # the shapes are timed on the workload itself: complete parallel solves
+    # take a fraction of a second each
+    (teams, threads), report = autotune.tune_search_shape(models, node_limit=0,
+                                                          deterministic=False)
     tune_s = time.perf_counter() - t0
     b = pccp.Batch(models, threads=threads, teams_per_cta=teams)
-    stream = torch.cuda.Stream()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(stream):
-        with torch.cuda.graph(graph, stream=stream):
-            b.solve_async(strategy=pccp.PCCP_FIRST_FAIL, stream=stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    graph.replay()
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    res = b.results(stream=stream)
-    nodes = sum(r["nodes"] for r in res)
-    per = sorted(r["model_ms"] for r in res)
-    return {"workload": f"{COMPLETE_MODELS} seeded models of {COMPLETE_FAMILY.replace('mixed', '')} "
-                        "tasks, 4 resources (config-2 distributions), first-fail, complete "
-                        "branch and bound, one team per model in the sequential order",
-            "complete": all(r["status"] == pccp.PCCP_RES_OPTIMAL for r in res), "graph": True,
-            "shape": {"teams_per_cta": teams, "threads": threads, "ctas": b.shape[2],
-                      "autotune_s": tune_s,
-                      "autotune_nodes_per_s": {f"{k[0]}x{k[1]}": v for k, v in report.items()}},
-            "ms_to_last_proof": ms, "nodes": nodes, "nodes_per_s": nodes / (ms / 1000),
-            "model_ms_to_proof": {"p50": per[len(per) // 2], "p99": per[int(0.99 * len(per)) - 1],
-                                  "max": per[-1], "sum": sum(per)},
-            "proven": sum(r["status"] == pccp.PCCP_RES_OPTIMAL for r in res),
-            "optima_sum": sum(r["objective"] for r in res)}
+    out = {"workload": f"{COMPLETE_MODELS} seeded models of "
+                       f"{COMPLETE_FAMILY.replace('mixed', '').replace('_', '-')} tasks, 4 resources "
+                       "(config-2 distributions), complete branch and bound to proven optima",
+           "graph": True,
+           "shape": {"teams_per_cta": teams, "threads": threads, "autotune_s": tune_s,
+                     "autotune_batches_per_s": {f"{k[0]}x{k[1]}": v for k, v in report.items()}}}
+    forms = [("first_fail", {"strategy": pccp.PCCP_FIRST_FAIL}),
+             ("input_order", {"strategy": pccp.PCCP_INPUT_ORDER})]
+    if policy is not None:
+        forms.append(("learned", {"strategy": pccp.PCCP_LEARNED, "policy": policy}))
+    optima = None
+    for name, kw in forms:
+        _graph_solve(pccp, b, deterministic=False, **kw)  # first replay pays the warm-up
+        ms, res = _graph_solve(pccp, b, deterministic=False, **kw)
+        out[name] = _proof_summary(pccp, ms, res)
+        obj = [r["objective"] for r in res]
+        assert optima is None or obj == optima, "optima differ between strategies"
+        optima = obj
+    out["optima_sum"] = sum(optima)
+    if policy is not None:
+        out["learned_vs_first_fail"] = {
+            "time_ratio": out["learned"]["ms_to_last_proof"] / out["first_fail"]["ms_to_last_proof"],
+            "node_ratio": out["learned"]["nodes"] / out["first_fail"]["nodes"],
+            "training": training}
+    if COMPLETE_SEQUENTIAL:
+        ms, res = _graph_solve(pccp, b, deterministic=True, strategy=pccp.PCCP_FIRST_FAIL)
+        out["first_fail_sequential_order"] = _proof_summary(pccp, ms, res)
+        assert [r["objective"] for r in res] == optima
+    return out
 
 
 def search_bench(pccp, cpu=True):
@@ -357,7 +392,10 @@ def search_bench(pccp, cpu=True):
         "solutions_found": sum(r["solutions"] for r in res),
         "iterations_per_node": sum(r["iterations"] for r in res) / max(nodes, 1)}}
     if COMPLETE_BATCH:
-        out["batched_complete"] = complete_batch_bench(pccp)
+        pol = training = None
+        if LEARNED_IN_BENCH:
+            pol, training = train_policy(argparse.Namespace(learned_epochs=8))
+        out["batched_complete"] = complete_batch_bench(pccp, pol, training)
     for key, fam, what in (("parallel", "j30", "30-task"), ("parallel_large", "j120", "120-task")):
         m = pccp.Model.from_rcpsp(config_instance(fam, 0))
         if EPS_NODE_LIMIT:

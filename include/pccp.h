@@ -235,9 +235,11 @@ typedef struct {
   int32_t strategy;      /* PCCP_INPUT_ORDER or PCCP_FIRST_FAIL */
   int32_t mode;          /* PCCP_OPTIMISE or PCCP_COUNT_ALL */
   int32_t deterministic; /* 1: one team walks the tree in the sequential DFS
-                            order, so node counts are reproducible; 0: many
-                            teams split the tree into subproblems and share
-                            the incumbent (node counts then vary) */
+                            order, so node counts are reproducible; 0: every
+                            team pulls subproblems from a shared queue, hands
+                            open branches to waiting teams and shares the
+                            incumbent (node counts then vary, except count-all
+                            and proof trees) */
   int32_t obj_ub;        /* inclusive upper bound told on the objective at every
                             node; INT32_MAX for none */
   int64_t node_limit;    /* stop after this many nodes (<= 0: none); per instance */
@@ -257,12 +259,12 @@ typedef struct {
   int32_t props_per_thread; /* propagator rows per thread per sweep: with threads == 0
                                the team size is the largest model's rows divided by
                                this, rounded up to whole warps (0 = not used) */
-  int32_t queue_granularity;/* parallel search: frontier subproblems per team before
-                               the persistent search starts (0 = 4) */
+  int32_t queue_granularity;/* parallel search: subproblems the queue keeps ready per
+                               waiting team; teams stop donating above it (0 = 1) */
   int32_t donate_nodes;     /* parallel search: after this many nodes in one
-                               subproblem a team hands its open right branches to the
-                               work queue while other teams wait for work
-                               (0 = the library's choice, < 0 = never) */
+                               subproblem a team hands its shallowest open right branch
+                               to the queue at each branching while teams wait for
+                               work (0 = the library's choice, 4; < 0 = never) */
 } pccp_solve_opts;
 
 /* Counters and outcome of one search.  A node is every store propagated,
@@ -289,14 +291,28 @@ typedef struct {
 } pccp_result;
 
 /* Solves one model.  Synchronous: returns after the result is filled.
+ * deterministic = 1: one team in the sequential order.  deterministic = 0:
+ * every team of the GPU over a shared queue of subproblems of the model (the
+ * EPS variant of Sec. 5 with work donation; see pccp_solve_batch), the
+ * table staged once per CTA when it fits; with stream_table and a table too
+ * large for shared memory, a breadth-first frontier of subproblems (about 4
+ * per team) is searched by persistent teams instead.
  * Errors: INVALID, SMEM, TIMEOUT (a device wait gave up), CUDA. */
 int pccp_solve(const pccp_model* model, const pccp_solve_opts* opts, pccp_result* result,
                void* stream);
 
-/* Solves n_models models in one persistent launch; each model is searched by
- * one team in the deterministic order (opts->deterministic is ignored and
- * node_limit / time_limit_ms apply per model), so every model's counts are
- * those of pccp_solve with deterministic = 1.  A CTA holds teams_per_cta
+/* Solves n_models models in one persistent launch.
+ * opts->deterministic = 1: each model is searched by one team in the
+ * sequential order (node_limit and time_limit_ms apply per model), so every
+ * model's counts are those of pccp_solve with deterministic = 1.
+ * opts->deterministic = 0: every team of the GPU works over one shared queue
+ * of subproblems (decision paths) of all the models, each model with its own
+ * shared incumbent; a team that has searched donate_nodes nodes of a
+ * subproblem while others wait hands its shallowest open right branch to the
+ * queue; node_limit applies per model and time_limit_ms to the whole launch.
+ * Optima, count-all counts and the counts of proof trees are exact in both
+ * forms; other node counts of the parallel form depend on timing.
+ * Deterministic form: a CTA holds teams_per_cta
  * teams side by side, each in its own slot of shared memory; the models are
  * queued largest table first and every team pulls the next one when it
  * finishes.  A model's table prefix is staged in its team's slot when it
@@ -327,15 +343,19 @@ int pccp_batch_create(const pccp_model* const* models, int32_t n_models, int32_t
 int pccp_batch_get_shape(const pccp_batch* batch, int32_t* threads, int32_t* teams_per_cta,
                          int32_t* ctas);
 
-/* Queues one search of every model of the batch on `stream` (deterministic
- * order, one team per model; same semantics and results as
- * pccp_solve_batch).  Enqueues only a memset and one kernel launch: no host
- * synchronisation and no allocation, so it may be captured in a CUDA graph
- * and replayed.  Calls on one batch must not overlap on the GPU. */
+/* Queues one search of every model of the batch on `stream`, with the same
+ * semantics and results as pccp_solve_batch: opts->deterministic = 1, one
+ * team per model in the sequential order (node counts reproducible);
+ * 0, every team over one shared queue of subproblems of all models with
+ * work donation.  Enqueues only memsets or an initialisation kernel and one
+ * search kernel: no host synchronisation and no allocation, so it may be
+ * captured in a CUDA graph and replayed.  Calls on one batch must not
+ * overlap on the GPU. */
 int pccp_batch_solve_async(pccp_batch* batch, const pccp_solve_opts* opts, void* stream);
 
-/* Synchronises `stream` and copies the last search's results (and the
- * witnesses of results[i].witness != NULL) to the host; elapsed_ms is 0. */
+/* Synchronises `stream` and copies the last queued search's results (and
+ * the witnesses of results[i].witness != NULL) to the host; elapsed_ms is 0
+ * (time the graph or the stream), model_ms is each model's own time. */
 int pccp_batch_results(pccp_batch* batch, pccp_result* results, void* stream);
 
 void pccp_batch_destroy(pccp_batch* batch);

@@ -339,11 +339,14 @@ def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, determini
 def solve_batch(models, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
                 node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None, noalloc=False,
                 skip_stable=None, policy=None, stream_table=False, teams_per_cta=0,
-                props_per_thread=0):
-    """Solve many models in one launch.  noalloc=True uses the allocation-free
-    entry point (fixed device scratch; see include/pccp.h)."""
-    o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, threads, blocks,
-              skip_stable, policy, stream_table, teams_per_cta, props_per_thread)
+                props_per_thread=0, deterministic=True, queue_granularity=0, donate_nodes=0):
+    """Solve many models in one launch.  deterministic=True: one team per
+    model in the sequential order; False: every team over one shared queue of
+    subproblems of all models, with work donation.  noalloc=True uses the
+    allocation-free entry point (fixed device scratch; see include/pccp.h)."""
+    o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
+              skip_stable, policy, stream_table, teams_per_cta, props_per_thread,
+              queue_granularity, donate_nodes)
     n = len(models)
     ws = [np.zeros(m.n_vars, dtype=np.int32) for m in models]
     res = (_abi.pccp_result * n)()
@@ -374,9 +377,10 @@ class Batch:
         return shp
 
     def solve_async(self, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
-                    node_limit=0, time_limit_ms=0, stream=None, skip_stable=None, policy=None):
-        o = _opts(strategy, mode, True, obj_ub, node_limit, time_limit_ms, 0, 0, skip_stable,
-                  policy)
+                    node_limit=0, time_limit_ms=0, stream=None, skip_stable=None, policy=None,
+                    deterministic=True, queue_granularity=0, donate_nodes=0):
+        o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, 0, 0,
+                  skip_stable, policy, False, 0, 0, queue_granularity, donate_nodes)
         check(pccp_batch_solve_async(self.handle, o, _stream_ptr(stream)), "pccp_batch_solve_async")
 
     def results(self, stream=None):

@@ -22,7 +22,7 @@ PROPAGATE_CANDIDATES = [(64, 4), (64, 8), (64, 15), (96, 5), (96, 10), (128, 2),
 SEARCH_THREADS = [64, 128, 256, 512]
 # batched search: (teams per CTA, threads per team); 0 threads = rows-based
 SEARCH_SHAPES = [(1, 256), (1, 512), (2, 256), (2, 512), (3, 256), (4, 128), (4, 256),
-                 (6, 128), (8, 128), (8, 64), (12, 64)]
+                 (6, 128), (8, 128), (8, 64), (12, 64), (15, 64), (15, 32)]
 # parallel search of one model: (frontier subproblems per team, donation node budget)
 EPS_CANDIDATES = [(2, 0), (4, 0), (8, 0), (4, -1), (16, -1)]
 
@@ -106,29 +106,36 @@ def tune_search_threads(models, node_limit=200, candidates=None, use_cache=True)
     return out
 
 
-def tune_search_shape(models, node_limit=300, candidates=None, strategy=None, use_cache=True):
+def tune_search_shape(models, node_limit=300, candidates=None, strategy=None, use_cache=True,
+                      deterministic=True):
     """Pick (teams_per_cta, threads) for a batched search of models like these:
-    each candidate solves the batch with a small node limit (deterministic
-    order, so every candidate does the same work) and the highest nodes/s of
-    device time wins.  Returns ((teams_per_cta, threads), report)."""
+    each candidate solves the batch with a node limit per model (in the
+    sequential order every candidate does the same work; in the parallel
+    form about the same; node_limit=0: complete solves, for batches that
+    finish quickly) and the highest nodes/s of device time (complete solves:
+    the shortest time, reported as proofs of the whole batch per second) wins.
+    Returns ((teams_per_cta, threads), report)."""
     from . import PCCP_FIRST_FAIL
     strategy = PCCP_FIRST_FAIL if strategy is None else strategy
-    key = ("shape", tuple(sorted(_shape_key(m) for m in models)), node_limit, strategy)
+    key = ("shape", tuple(sorted(_shape_key(m) for m in models)), node_limit, strategy,
+           deterministic)
     if use_cache and key in _cache:
         return _cache[key]
     report = {}
     best = None
     for teams, threads in (candidates or SEARCH_SHAPES):
         try:
-            solve_batch(models, node_limit=max(1, node_limit // 8), threads=threads,
-                        teams_per_cta=teams, strategy=strategy)
+            solve_batch(models, node_limit=max(1, node_limit // 8) if node_limit else 0,
+                        threads=threads, teams_per_cta=teams, strategy=strategy,
+                        deterministic=deterministic)
             r = solve_batch(models, node_limit=node_limit, threads=threads, teams_per_cta=teams,
-                            strategy=strategy)
+                            strategy=strategy, deterministic=deterministic)
         except PccpError:
             report[(teams, threads)] = None
             continue
         ms = r[0]["elapsed_ms"]
-        rate = sum(x["nodes"] for x in r) / (ms / 1000.0)
+        # node-limited runs: nodes/s; complete runs: 1 / time to the last proof
+        rate = sum(x["nodes"] for x in r) / (ms / 1000.0) if node_limit else 1000.0 / ms
         report[(teams, threads)] = rate
         if best is None or rate > best[0]:
             best = (rate, (teams, threads))

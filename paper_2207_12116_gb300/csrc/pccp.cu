@@ -461,6 +461,8 @@ __global__ void __launch_bounds__(1024) k_solve_slots(SolveArgs a) {
   }
 }
 
+#include "k_search_queue.inc"
+
 // -------------------------------------------------------------- host model
 
 struct Packed {
@@ -1416,6 +1418,11 @@ SolveArgs batch_args(const BatchPlan& p, const pccp_solve_opts* o, int32_t n) {
   return a;
 }
 
+// Parallel search over a shared queue of subproblems (defined with the
+// parallel search entry points below).
+int solve_queue(const pccp_model* const* models, int32_t n, const pccp_solve_opts* o,
+                pccp_result* results, cudaStream_t s);
+
 }  // namespace
 
 extern "C" {
@@ -1616,6 +1623,14 @@ int pccp_solve_batch(const pccp_model* const* models, int32_t n_models,
   {
     const int rc0 = check_strategy(opts);
     if (rc0 != PCCP_OK) return rc0;
+  }
+  if (!opts->deterministic) {  // every team over one shared queue of subproblems
+    for (int32_t i = 0; i < n_models; ++i) {
+      if (!models[i]) return PCCP_ERR_INVALID;
+      const int rc = check_device(models[i]);
+      if (rc != PCCP_OK) return rc;
+    }
+    return solve_queue(models, n_models, opts, results, static_cast<cudaStream_t>(stream));
   }
   std::vector<InstanceDesc> desc(n_models);
   std::vector<int32_t> woff(n_models);
@@ -1954,6 +1969,296 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
 
 }  // namespace
 
+namespace {
+
+// Launch plan of the parallel search over the shared queue.
+struct QueuePlan {
+  void (*kern)(QArgs);
+  int team, teams, grid, max_len, xw;
+  size_t smem;
+  uint32_t slot_bytes, off_track, off_x, off_stack, off_store;
+  bool shared, table_global;
+  uint32_t shared_bytes, shared_region;
+};
+
+template <int kMode>
+void (*queue_kernel_t(const pccp_solve_opts* o))(QArgs) {
+  if (o->strategy == PCCP_LEARNED) return k_search_queue<false, false, true, kMode>;
+  if (o->skip_stable > 0) return k_search_queue<true, true, false, kMode>;
+  if (o->skip_stable < 0) return k_search_queue<false, false, false, kMode>;
+  return k_search_queue<false, true, false, kMode>;
+}
+// mode 0: a slot per team (many models); 1: one model, table shared in the
+// CTA; 2: one model, table read in place
+void (*queue_kernel(const pccp_solve_opts* o, int mode))(QArgs) {
+  return mode == 0 ? queue_kernel_t<0>(o) : mode == 1 ? queue_kernel_t<1>(o) : queue_kernel_t<2>(o);
+}
+
+// Team size of a search when the caller leaves it to the library: enough
+// threads for about two rows each of the largest model, in whole warps, at
+// least 64 and at most `cap` (small models: small teams, so more of them).
+int default_team(int max_rows, int cap) {
+  return std::min(cap, std::max(64, ((max_rows + 1) / 2 + 31) & ~31));
+}
+
+int plan_queue(const pccp_model* const* models, int32_t n, const pccp_solve_opts* o,
+               QueuePlan* p, bool any_strategy = false) {
+  const int smem_max = max_dyn_smem();
+  const int sms = sm_count();
+  if (smem_max <= 0 || sms <= 0) return PCCP_ERR_CUDA;
+  if (o->threads < 0 || o->threads % 32 != 0 || o->threads > 1024) return PCCP_ERR_INVALID;
+  if (o->teams_per_cta < 0 || o->teams_per_cta > kMaxTeamsPerCta) return PCCP_ERR_INVALID;
+  int32_t max_vars = 0, max_branch = 0, max_tw = 0, max_rows = 0, max_dec = 2;
+  for (int32_t i = 0; i < n; ++i) {
+    const pccp_model* m = models[i];
+    max_vars = std::max(max_vars, m->n_vars);
+    max_branch = std::max(max_branch, m->n_branch);
+    max_tw = std::max(max_tw, track_words(m->n_vars, m->n_lin));
+    max_rows = std::max(max_rows, m->n_t + m->n_rf + m->n_lin);
+    max_dec = std::max(max_dec, m->max_decisions);
+  }
+  p->xw = any_strategy ? 8 * ((max_branch + 15) & ~15) : policy_x_words(o, max_branch);
+  p->max_len = max_dec;
+  p->off_track = static_cast<uint32_t>(align16(16 + sizeof(QCtrl)));
+  p->off_x = p->off_track + 4u * static_cast<uint32_t>((max_tw + 3) & ~3);
+  p->off_stack = static_cast<uint32_t>(align16(p->off_x + 4u * static_cast<uint32_t>(p->xw)));
+  p->off_store = static_cast<uint32_t>(
+      align16(p->off_stack + sizeof(int2) * static_cast<size_t>(p->max_len)));
+  const bool learned = o->strategy == PCCP_LEARNED;
+  const bool track_s = !learned && o->skip_stable > 0;
+  p->shared = n == 1;
+  if (p->shared) {
+    // one model: its table once per CTA, shared by the CTA's teams
+    const pccp_model* m = models[0];
+    const uint32_t per = static_cast<uint32_t>(
+        (p->off_store + 8ull * static_cast<uint32_t>(m->n_vars) + 127u) & ~127ull);
+    const uint32_t img = track_s ? m->track_bytes : m->core_bytes;
+    const uint32_t region = ((img + 127u) & ~127u) + 128u;
+    p->table_global = static_cast<size_t>(region) + per > static_cast<size_t>(smem_max);
+    if (per > static_cast<uint32_t>(smem_max)) return PCCP_ERR_SMEM;
+    p->shared_bytes = p->table_global ? 0u : img;
+    p->shared_region = p->table_global ? 0u : region;
+    int team = o->threads;
+    if (team == 0 && o->props_per_thread > 0)
+      team = std::min(1024, std::max(32, ((max_rows + o->props_per_thread - 1) /
+                                              o->props_per_thread + 31) & ~31));
+    if (team == 0) team = p->table_global ? 1024 : default_team(max_rows, 128);
+    const int fit = static_cast<int>((static_cast<uint32_t>(smem_max) - p->shared_region) / per);
+    int teams = o->teams_per_cta > 0 ? o->teams_per_cta : 8;
+    teams = std::min({teams, fit, 1024 / team});
+    if (teams < 1 || (o->teams_per_cta > 0 && teams < o->teams_per_cta)) return PCCP_ERR_SMEM;
+    p->team = team;
+    p->teams = teams;
+    p->slot_bytes = per;
+    p->smem = p->shared_region + static_cast<size_t>(teams) * per;
+    p->kern = queue_kernel(o, p->table_global ? 2 : 1);
+  } else {
+    // many models: a slot per team, as the batched search plans them
+    pccp_solve_opts q = *o;
+    if (q.threads == 0 && q.props_per_thread == 0) q.threads = default_team(max_rows, 256);
+    BatchPlan bp;
+    const int rc = plan_batch(models, n, &q, false, &bp);
+    if (rc != PCCP_OK) return rc;
+    if (!bp.slots) return PCCP_ERR_INVALID;  // streaming is not offered here
+    // the same choices with this kernel's control block
+    const int teams = bp.teams;
+    const uint32_t room = static_cast<uint32_t>(smem_max / teams) & ~127u;
+    uint32_t want = 0;
+    for (int32_t i = 0; i < n; ++i) {
+      const uint32_t staged = slot_need(models[i], p->off_store, track_s, true);
+      want = std::max(want, staged <= room ? staged
+                                           : slot_need(models[i], p->off_store, false, false));
+    }
+    if (want > room) return PCCP_ERR_SMEM;
+    p->shared_bytes = p->shared_region = 0;
+    p->table_global = false;
+    p->team = bp.team;
+    p->teams = teams;
+    p->slot_bytes = (want + 127u) & ~127u;
+    p->smem = static_cast<size_t>(teams) * p->slot_bytes;
+    p->kern = queue_kernel(o, 0);
+  }
+  void (*kerns[8])(QArgs) = {p->kern};
+  int n_kerns = 1;
+  if (any_strategy) {  // a batch planned once for every later search
+    pccp_solve_opts q = *o;
+    const int mode = p->shared ? (p->table_global ? 2 : 1) : 0;
+    for (int strategy : {PCCP_INPUT_ORDER, PCCP_LEARNED})
+      for (int skip : {-1, 0, 1}) {
+        q.strategy = strategy;
+        q.skip_stable = skip;
+        if (n_kerns < 8) kerns[n_kerns++] = queue_kernel(&q, mode);
+      }
+  }
+  int per_sm = 1 << 30;
+  for (int ki = 0; ki < n_kerns; ++ki) {
+    PCCP_CUDA(allow_smem(reinterpret_cast<const void*>(kerns[ki]), p->smem));
+    int occ = 0;
+    PCCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kerns[ki], p->team * p->teams,
+                                                            p->smem));
+    per_sm = std::min(per_sm, occ);
+  }
+  if (per_sm < 1) return PCCP_ERR_SMEM;
+  p->grid = sms * per_sm;
+  if (o->blocks > 0) p->grid = std::min(p->grid, static_cast<int>(o->blocks));
+  return PCCP_OK;
+}
+
+// Ring capacity of a queue search: every root, then room for donations.
+size_t queue_cap(int32_t n, int n_teams, int max_len) {
+  const size_t per_item = static_cast<size_t>(max_len) * sizeof(int2);
+  return std::max<size_t>(static_cast<size_t>(n) + 2 * static_cast<size_t>(n_teams),
+                          std::min<size_t>(65536, (96u << 20) / per_item));
+}
+
+// Option-dependent kernel arguments of a queue search.
+void queue_opts_args(const pccp_solve_opts* o, QArgs* a) {
+  a->policy = o->strategy == PCCP_LEARNED ? policy_dev(o->policy) : nullptr;
+  a->mode = o->mode;
+  a->strategy = o->strategy;
+  a->obj_ub = o->obj_ub;
+  a->donate_nodes = o->donate_nodes < 0 ? -1 : (o->donate_nodes > 0 ? o->donate_nodes : 4);
+  a->granularity = o->queue_granularity > 0 ? o->queue_granularity : 1;
+  a->node_limit = o->node_limit;
+  a->time_limit_ns = o->time_limit_ms > 0 ? o->time_limit_ms * 1000000ll : 0;
+}
+
+// Results of a queue search from the per-model states.
+int queue_results(const pccp_model* const* models, int32_t n, const QModel* hq,
+                  const QGlobal& hg, const int32_t* hwit, const int32_t* woff, float ms,
+                  pccp_result* results) {
+  for (int32_t i = 0; i < n; ++i) {
+    const QModel& q = hq[i];
+    pccp_result& r = results[i];
+    const bool has = q.has != 0;
+    r.has_solution = has;
+    r.objective = has ? q.wit_obj : 0;
+    // complete: satisfied, or every item of the model exhausted untouched by
+    // a limit (items left in the queue by a stop keep outstanding above 0)
+    if (q.done == 1 || (q.outstanding == 0 && !q.cut && hg.error == 0))
+      r.status = has ? PCCP_RES_OPTIMAL : PCCP_RES_INFEASIBLE;
+    else
+      r.status = PCCP_RES_LIMIT;
+    r.nodes = static_cast<int64_t>(q.nodes);
+    r.fails = static_cast<int64_t>(q.fails);
+    r.solutions = static_cast<int64_t>(q.sols);
+    r.iterations = static_cast<int64_t>(q.iters);
+    r.rows_evaluated = static_cast<int64_t>(q.evals);
+    r.max_depth = q.max_depth;
+    r.elapsed_ms = ms;
+    r.model_ms = q.outstanding == 0 ? static_cast<float>(q.t_done) * 1e-6f : 0.f;
+    if (r.witness && has && hwit)
+      std::memcpy(r.witness, hwit + woff[i],
+                  static_cast<size_t>(models[i]->n_vars) * sizeof(int32_t));
+  }
+  if (hg.error == 1 || hg.error == 3 || hg.error == 4) return PCCP_ERR_TIMEOUT;
+  if (hg.error == 2) return PCCP_ERR_INVALID;
+  return PCCP_OK;
+}
+
+// Plan-dependent kernel arguments of a queue search.
+void queue_plan_args(const QueuePlan& plan, int32_t n, size_t cap, QArgs* a) {
+  a->n_models = n;
+  a->cap = static_cast<int>(cap);
+  a->max_len = plan.max_len;
+  a->n_teams = plan.grid * plan.teams;
+  a->team_size = plan.team;
+  a->teams = plan.teams;
+  a->slot_bytes = plan.slot_bytes;
+  a->off_track = plan.off_track;
+  a->off_x = plan.off_x;
+  a->off_stack = plan.off_stack;
+  a->off_store = plan.off_store;
+  a->shared_table = plan.shared ? 1 : 0;
+  a->table_global = plan.table_global ? 1 : 0;
+  a->shared_bytes = plan.shared_bytes;
+  a->shared_region = plan.shared_region;
+}
+
+// Parallel search of n models over one shared queue (see k_search_queue.inc).
+int solve_queue(const pccp_model* const* models, int32_t n, const pccp_solve_opts* o,
+                pccp_result* results, cudaStream_t s) {
+  QueuePlan plan;
+  int rc = plan_queue(models, n, o, &plan);
+  if (rc != PCCP_OK) return rc;
+  const int n_teams = plan.grid * plan.teams;
+  std::vector<InstanceDesc> desc(n);
+  std::vector<int32_t> woff(n);
+  int64_t wit_total = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    woff[i] = static_cast<int32_t>(wit_total);
+    wit_total += models[i]->n_vars;
+    if (wit_total > INT32_MAX) return PCCP_ERR_INVALID;
+    desc[i] = instance_desc(models[i], i, woff[i]);
+  }
+  const size_t per_item = static_cast<size_t>(plan.max_len) * sizeof(int2);
+  const size_t cap = queue_cap(n, n_teams, plan.max_len);
+  if (cap > static_cast<size_t>(INT32_MAX)) return PCCP_ERR_INVALID;
+  const size_t o_g = 0;
+  const size_t o_qm = align16(o_g + sizeof(QGlobal));
+  const size_t o_desc = align16(o_qm + static_cast<size_t>(n) * sizeof(QModel));
+  const size_t o_seq = align16(o_desc + static_cast<size_t>(n) * sizeof(InstanceDesc));
+  const size_t o_hdr = align16(o_seq + cap * sizeof(unsigned long long));
+  const size_t o_path = align16(o_hdr + cap * sizeof(int2));
+  const size_t o_wit = align16(o_path + cap * per_item);
+  const size_t total = align16(o_wit + static_cast<size_t>(wit_total) * sizeof(int32_t));
+  uint8_t* d = nullptr;
+  PCCP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), total, s));
+  QArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.inst = reinterpret_cast<const InstanceDesc*>(d + o_desc);
+  a.qm = reinterpret_cast<QModel*>(d + o_qm);
+  a.g = reinterpret_cast<QGlobal*>(d + o_g);
+  a.seq = reinterpret_cast<unsigned long long*>(d + o_seq);
+  a.hdr = reinterpret_cast<int2*>(d + o_hdr);
+  a.path = reinterpret_cast<int2*>(d + o_path);
+  a.witness = reinterpret_cast<int32_t*>(d + o_wit);
+  queue_plan_args(plan, n, cap, &a);
+  queue_opts_args(o, &a);
+  std::vector<QModel> hq(n);
+  QGlobal hg;
+  std::vector<int32_t> hwit(static_cast<size_t>(wit_total));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  rc = PCCP_OK;
+  do {
+    if (cudaMemcpyAsync(d + o_desc, desc.data(), desc.size() * sizeof(InstanceDesc),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      rc = PCCP_ERR_CUDA;
+      break;
+    }
+    k_queue_init<<<256, 256, 0, s>>>(a);
+    cudaEventRecord(e0, s);
+    plan.kern<<<plan.grid, plan.team * plan.teams, plan.smem, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) {
+      rc = PCCP_ERR_CUDA;
+      break;
+    }
+    cudaEventRecord(e1, s);
+    if (cudaMemcpyAsync(hq.data(), d + o_qm, hq.size() * sizeof(QModel), cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaMemcpyAsync(&hg, d + o_g, sizeof(hg), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hwit.data(), d + o_wit, hwit.size() * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = PCCP_ERR_CUDA;
+      break;
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(d, s);
+  if (rc != PCCP_OK) {
+    (void)cudaGetLastError();
+    return rc;
+  }
+  return queue_results(models, n, hq.data(), hg, hwit.data(), woff.data(), ms, results);
+}
+
+}  // namespace
+
 extern "C" {
 
 int pccp_solve(const pccp_model* m, const pccp_solve_opts* opts, pccp_result* result,
@@ -1966,7 +2271,16 @@ int pccp_solve(const pccp_model* m, const pccp_solve_opts* opts, pccp_result* re
   if (!opts->deterministic) {
     const int rc = check_device(m);
     if (rc != PCCP_OK) return rc;
-    return solve_parallel(m, opts, result, static_cast<cudaStream_t>(stream));
+    // streamed tables keep the frontier-then-persistent search
+    // (k_eps_expand / k_eps_solve); otherwise the shared queue with donation
+    if (opts->stream_table > 0) {
+      const int smem_max = max_dyn_smem();
+      if (smem_max <= 0) return PCCP_ERR_CUDA;
+      if (static_cast<int64_t>(m->core_bytes) + 128 + 8ll * m->n_vars + 4096 > smem_max)
+        return solve_parallel(m, opts, result, static_cast<cudaStream_t>(stream));
+    }
+    const pccp_model* one[1] = {m};
+    return solve_queue(one, 1, opts, result, static_cast<cudaStream_t>(stream));
   }
   pccp_solve_opts o = *opts;
   if (o.threads <= 0) o.threads = 512;
