@@ -652,6 +652,32 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile_leg(args):
+    """One warm-up launch and one launch of a search kernel, for ncu captures
+    (skip 1 launch of the kernel, capture 1):
+      batched : k_solve_slots, 256 seeded 30-60-task models, input order,
+                500 nodes each, the library's launch shape;
+      complete: k_search_queue, the 256 6-10-task models proved optimal in
+                the parallel form, first-fail, 8 teams of 64 threads per CTA."""
+    import torch
+    import paper_2207_12116_gb300 as pccp
+    from synthetic import config_instance
+    torch.cuda.set_device(0)
+    if args.profile_leg == "batched":
+        models = [pccp.Model.from_rcpsp(config_instance("mixed30_60", s)) for s in range(256)]
+        pccp.solve_batch(models[:8], node_limit=50)
+        r = pccp.solve_batch(models, node_limit=500)
+    else:
+        models = [pccp.Model.from_rcpsp(config_instance(COMPLETE_FAMILY, s))
+                  for s in range(COMPLETE_MODELS)]
+        kw = dict(strategy=pccp.PCCP_FIRST_FAIL, deterministic=False, teams_per_cta=8, threads=64)
+        pccp.solve_batch(models[:4], **kw)
+        r = pccp.solve_batch(models, **kw)
+    print(json.dumps({"leg": args.profile_leg, "ms": r[0]["elapsed_ms"],
+                      "nodes": sum(x["nodes"] for x in r),
+                      "rows": sum(x["rows_evaluated"] for x in r)}), flush=True)
+
+
 def run_search_only(args):
     """Only the search leg (used for ncu captures of the search kernels)."""
     import torch
@@ -827,6 +853,8 @@ def main():
     ap.add_argument("--search-only", action="store_true",
                     help="small search leg only (64 models x 500 nodes; parallel runs "
                          "stopped after 2,000,000 nodes)")
+    ap.add_argument("--profile-leg", choices=["batched", "complete"], default="",
+                    help="one warm-up and one measured launch of a search kernel (ncu captures)")
     ap.add_argument("--team", type=int, default=0, help="threads per team (0: library default)")
     ap.add_argument("--teams", type=int, default=0, help="teams per CTA (0: library default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
@@ -840,6 +868,8 @@ def main():
         N_NODES = args.nodes
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_leg:
+        run_profile_leg(args)
     elif args.search_only:
         run_search_only(args)
     elif args.learned:
