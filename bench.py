@@ -362,6 +362,16 @@ def complete_batch_bench(pccp, policy=None, training=None):
             "time_ratio": out["learned"]["ms_to_last_proof"] / out["first_fail"]["ms_to_last_proof"],
             "node_ratio": out["learned"]["nodes"] / out["first_fail"]["nodes"],
             "training": training}
+    # the plain form without batching: one parallel search per model, one
+    # after another (device time summed; host wall time of the loop)
+    t0 = time.perf_counter()
+    one = [pccp.solve(m, strategy=pccp.PCCP_FIRST_FAIL, deterministic=False) for m in models]
+    wall = time.perf_counter() - t0
+    assert [r["objective"] for r in one] == optima
+    out["first_fail_one_model_at_a_time"] = {
+        "device_ms_sum": sum(r["elapsed_ms"] for r in one), "wall_ms": 1000 * wall,
+        "nodes": sum(r["nodes"] for r in one),
+        "proven": sum(r["status"] == pccp.PCCP_RES_OPTIMAL for r in one)}
     if COMPLETE_SEQUENTIAL:
         ms, res = _graph_solve(pccp, b, deterministic=True, strategy=pccp.PCCP_FIRST_FAIL)
         out["first_fail_sequential_order"] = _proof_summary(pccp, ms, res)
@@ -394,7 +404,7 @@ def search_bench(pccp, cpu=True):
     if COMPLETE_BATCH:
         pol = training = None
         if LEARNED_IN_BENCH:
-            pol, training = train_policy(argparse.Namespace(learned_epochs=8))
+            pol, training = train_policy_rollouts()
         out["batched_complete"] = complete_batch_bench(pccp, pol, training)
     for key, fam, what in (("parallel", "j30", "30-task"), ("parallel_large", "j120", "120-task")):
         m = pccp.Model.from_rcpsp(config_instance(fam, 0))
@@ -686,6 +696,33 @@ def run_search_only(args):
     global SEARCH_MODELS, SEARCH_NODE_LIMIT, EPS_NODE_LIMIT, COMPLETE_BATCH
     SEARCH_MODELS, SEARCH_NODE_LIMIT, EPS_NODE_LIMIT, COMPLETE_BATCH = 64, 500, 2_000_000, False
     print(json.dumps(search_bench(pccp, cpu=False)), flush=True)
+
+
+ROLLOUT_TRAIN_SEEDS = range(5000, 5096)  # disjoint from the complete batch's seeds 0..255
+
+
+def train_policy_rollouts():
+    """A learned-branching policy for the complete-solve family, trained on
+    96 other seeded 6-10-task models: proof-phase nodes labelled by the
+    measured first-fail proof sizes below each candidate's split, with
+    first-fail's width preference as a prior (soft targets, T = 0.5, width
+    weight 0.5), 30 epochs.  Returns (policy, training summary)."""
+    import paper_2207_12116_gb300 as pccp
+    from paper_2207_12116_gb300 import learn
+    t0 = time.perf_counter()
+    insts = [config_instance(COMPLETE_FAMILY, s) for s in ROLLOUT_TRAIN_SEEDS]
+    data, stats = learn.collect_rollouts(insts, nodes_per_model=32, seed=1)
+    t1 = time.perf_counter()
+    learn.rollout_targets(data, "soft_ff", 0.5, 0.5)
+    pol = pccp.Policy.random(0)
+    losses = learn.train(pol, data, epochs=30, groups_per_batch=64, lr=2e-3)
+    return pol, {"labels": "first-fail proof sizes below each candidate's split (rollouts), "
+                           "soft targets with a first-fail width prior",
+                 "train_models": f"{COMPLETE_FAMILY} seeds {ROLLOUT_TRAIN_SEEDS.start}-"
+                                 f"{ROLLOUT_TRAIN_SEEDS.stop - 1}",
+                 **stats, "epochs": 30, "loss_first_last": [losses[0], losses[-1]],
+                 "top1_accuracy": learn.ranking_accuracy(pol, data),
+                 "collect_s": t1 - t0, "seconds": time.perf_counter() - t0}
 
 
 def train_policy(args):

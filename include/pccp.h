@@ -392,9 +392,10 @@ int pccp_solve_batch_noalloc(const pccp_model* const* models, int32_t n_models,
 /* ---- learned branching (no counterpart in the paper) --------------------
  * A policy is an MLP 12 -> 128 -> 128 -> 1 (ReLU) that scores each unfixed
  * branch variable of a node from 12 features (its bounds relative to the
- * root, log width, temporal in/out degree and summed offsets, reified and
- * linear rows touching it, its input position, the depth and the
- * objective's progress).  The search splits the highest-scoring variable
+ * root, log width, temporal in/out degree and summed offsets, reified rows
+ * touching it, its demand on the linear rows (for a task's start time: the
+ * sum over resources of usage / capacity), its input position, the depth
+ * and the objective's progress).  The search splits the highest-scoring variable
  * (ties to the lower index) with the usual lower-half rule, so a complete
  * search still proves the same optimum; only the order of the tree changes.
  * Weights are BF16 on the device (FP32 masters for training); every product
@@ -415,6 +416,12 @@ void pccp_policy_destroy(pccp_policy* policy);
 /* Current FP32 weights into caller HOST arrays of the sizes above. */
 int pccp_policy_get_weights(const pccp_policy* policy, float* w1, float* b1, float* w2, float* b2,
                             float* w3, float* b3);
+/* Gradient of the mean loss of the last pccp_policy_train_step (the step
+ * Adam then took) with respect to the FP32 parameters, into caller HOST
+ * arrays of the shapes above.  Synchronises the device.  INVALID before the
+ * first step. */
+int pccp_policy_get_gradients(const pccp_policy* policy, float* w1, float* b1, float* w2,
+                              float* b2, float* w3, float* b3);
 /* Features of every branch variable of n_stores stores (DEVICE lb/ub
  * [n_stores][n_vars], joined with the root; depth DEVICE [n_stores] or NULL
  * for 0) into DEVICE out [n_stores][n_branch][12], rounded to BF16 as the

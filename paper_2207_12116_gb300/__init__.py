@@ -28,6 +28,7 @@ __all__ = ["Model", "pccp_model_create", "pccp_model_destroy", "pccp_model_get_i
            "pccp_solve_batch_noalloc", "pccp_batch_create", "pccp_batch_solve_async",
            "pccp_batch_results", "pccp_batch_destroy", "pccp_batch_get_shape", "Batch", "Policy",
            "pccp_policy_create", "pccp_policy_destroy", "pccp_policy_get_weights",
+           "pccp_policy_get_gradients",
            "pccp_policy_features", "pccp_policy_score", "pccp_policy_train_step",
            "pccp_error_string", "propagate", "propagate_host", "pccp_propagate_host", "solve",
            "solve_batch",
@@ -419,6 +420,10 @@ def pccp_policy_get_weights(handle, w1, b1, w2, b2, w3, b3):
     return load().pccp_policy_get_weights(handle, w1, b1, w2, b2, w3, b3)
 
 
+def pccp_policy_get_gradients(handle, w1, b1, w2, b2, w3, b3):
+    return load().pccp_policy_get_gradients(handle, w1, b1, w2, b2, w3, b3)
+
+
 def pccp_policy_features(model_handle, n, lb, ub, depth, out, stream):
     return load().pccp_policy_features(model_handle, n, lb, ub, depth, out, stream)
 
@@ -458,15 +463,22 @@ class Policy:
                     "b2": np.zeros(128), "w3": g.normal(0, scale * np.sqrt(1 / 128), 128),
                     "b3": 0.0})
 
-    def weights(self):
+    def _params(self, call, name):
         out = {k: np.zeros(shape, dtype=np.float32) for k, shape in POLICY_SHAPES.items()}
         b3 = np.zeros(1, dtype=np.float32)
-        rc = pccp_policy_get_weights(self.handle, *[ctypes.c_void_p(out[k].ctypes.data)
-                                                    for k in ("w1", "b1", "w2", "b2", "w3")],
-                                     ctypes.c_void_p(b3.ctypes.data))
-        check(rc, "pccp_policy_get_weights")
+        rc = call(self.handle, *[ctypes.c_void_p(out[k].ctypes.data)
+                                 for k in ("w1", "b1", "w2", "b2", "w3")],
+                  ctypes.c_void_p(b3.ctypes.data))
+        check(rc, name)
         out["b3"] = float(b3[0])
         return out
+
+    def weights(self):
+        return self._params(pccp_policy_get_weights, "pccp_policy_get_weights")
+
+    def gradients(self):
+        """Gradient of the last training step's mean loss (weight shapes)."""
+        return self._params(pccp_policy_get_gradients, "pccp_policy_get_gradients")
 
     def score(self, features, stream=None):
         """Scores of feature rows (float32 CUDA tensor [n, 12]) -> CUDA tensor [n]."""

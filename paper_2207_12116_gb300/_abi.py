@@ -97,6 +97,7 @@ SIGNATURES = {
     "pccp_policy_create": (ctypes.c_int, [ctypes.POINTER(pccp_policy_weights), ctypes.POINTER(P)]),
     "pccp_policy_destroy": (None, [P]),
     "pccp_policy_get_weights": (ctypes.c_int, [P, P, P, P, P, P, P]),
+    "pccp_policy_get_gradients": (ctypes.c_int, [P, P, P, P, P, P, P]),
     "pccp_policy_features": (ctypes.c_int, [P, I32, P, P, P, P, P]),
     "pccp_policy_score": (ctypes.c_int, [P, I32, P, P, P]),
     "pccp_policy_train_step": (ctypes.c_int, [P, I32, P, P, I32, P, ctypes.c_float,

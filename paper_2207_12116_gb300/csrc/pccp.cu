@@ -835,6 +835,22 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   std::vector<BranchStatic> BST(d->n_branch);
   {
     std::vector<float> out_deg(nv, 0.f), sum_d(nv, 0.f), in_deg(nv, 0.f), n_rf(nv, 0.f);
+    // demand: for the x of each reified row b <=> (x <= y < x + d), the
+    // linear rows holding b with a positive bound add coef / bound; the
+    // feature is the mean over those reified rows (for a scheduling start
+    // variable s_i: the sum over resources of r_{k,i} / c_k)
+    std::vector<double> dem_b(nv, 0.0), dem_acc(nv, 0.0);
+    std::vector<int32_t> dem_cnt(nv, 0);
+    for (int32_t i = 0; i < d->n_linear; ++i) {
+      if (d->linear_c[i] <= 0) continue;
+      for (int32_t k = d->linear_off[i]; k < d->linear_off[i + 1]; ++k)
+        if (d->term_coef[k] > 0)
+          dem_b[d->term_var[k]] += static_cast<double>(d->term_coef[k]) / d->linear_c[i];
+    }
+    for (int32_t i = 0; i < d->n_reified; ++i) {
+      dem_acc[d->reified[4 * i + 1]] += dem_b[d->reified[4 * i]];
+      dem_cnt[d->reified[4 * i + 1]] += 1;
+    }
     for (int32_t i = 0; i < d->n_temporal; ++i) {
       out_deg[d->temporal[3 * i]] += 1.f;
       sum_d[d->temporal[3 * i]] += static_cast<float>(d->temporal[3 * i + 2]);
@@ -852,7 +868,7 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
       bsk.sum_d = sum_d[v];
       bsk.in_deg = in_deg[v];
       bsk.n_reified = n_rf[v];
-      bsk.n_linear = static_cast<float>(by_var[v].size());
+      bsk.demand = dem_cnt[v] ? static_cast<float>(dem_acc[v] / dem_cnt[v]) : 0.f;
       BST[k] = bsk;
     }
   }

@@ -179,6 +179,19 @@ __device__ __forceinline__ bool team_bar_or(int id, int n, bool p) {
   return r != 0;
 }
 
+// Named barrier over `n` threads returning how many of them passed p.
+__device__ __forceinline__ int team_bar_popc(int id, int n, bool p) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred pi;\n\t"
+      "setp.ne.s32 pi, %1, 0;\n\t"
+      "bar.red.popc.u32 %0, %2, %3, pi;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<int>(p)), "r"(id), "r"(n)
+      : "memory");
+  return r;
+}
+
 __device__ __forceinline__ void team_bar(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }

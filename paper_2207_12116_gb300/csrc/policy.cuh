@@ -37,9 +37,12 @@ struct PolicyDev {
 
 // Static features of the branch variables (per model, in the table image):
 // out-degree and summed offsets of temporal rows (x), in-degree (y), reified
-// rows touching the variable, linear rows holding it.
+// rows touching the variable, and its demand: the mean, over the reified
+// rows b <=> (v <= y < v + d), of the sum of coef / bound over the linear
+// rows holding b (for a task's start time: its total demand, the sum over
+// resources of usage / capacity).
 struct BranchStatic {
-  float out_deg, sum_d, in_deg, n_reified, n_linear, pad[3];
+  float out_deg, sum_d, in_deg, n_reified, demand, pad[3];
 };
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -59,7 +62,7 @@ __device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4],
 // at a node, written as 16 bf16 (4 zero pads) into `row` (8 words).
 //   0 (lb - lb0) / (w0 + 1)     1 (ub - lb0) / (w0 + 1)    2 (ub - lb) / (w0 + 1)
 //   3 log2(1 + ub - lb) / 16    4 out-degree / 8           5 summed offsets / (w0 + 1)
-//   6 in-degree / 8             7 reified rows / 64         8 linear rows / 16
+//   6 in-degree / 8             7 reified rows / 64         8 demand / 4
 //   9 k / n_branch              10 depth / (depth + 32)    11 objective progress
 // (w0 = root width of the variable; objective progress = (lb(obj) - lb0(obj))
 // / (root width of obj + 1), 0 without an objective.)
@@ -75,7 +78,7 @@ __device__ __forceinline__ void write_features(uint32_t* row, int k, int2 D, int
   const float f5 = s.sum_d * inv;
   const float f6 = s.in_deg * 0.125f;
   const float f7 = s.n_reified * (1.0f / 64.0f);
-  const float f8 = s.n_linear * (1.0f / 16.0f);
+  const float f8 = s.demand * 0.25f;
   const float f9 = static_cast<float>(k) / static_cast<float>(n_branch);
   const float f10 = static_cast<float>(depth) / (static_cast<float>(depth) + 32.0f);
   row[0] = pack_bf16x2(f0, f1);
@@ -164,15 +167,27 @@ __device__ __forceinline__ void learned_select(const Tab& tb, int2* st,
     prog = static_cast<float>(ld_dom(st, tb.objective).x - RO.x) /
            (static_cast<float>(RO.y - RO.x) + 1.f);
   }
+  int n_open = 0, last = -1;  // unfixed candidates of this thread
   for (int k = tm.tid; k < nbp; k += tm.nthr) {
     if (k < nb) {
       const int v = tb.branch[k];
-      write_features(X + 8 * k, k, ld_dom(st, v), __ldg(root + v), bs[k], nb, depth, prog);
+      const int2 D = ld_dom(st, v);
+      if (D.x < D.y) {
+        ++n_open;
+        last = k;
+      }
+      write_features(X + 8 * k, k, D, __ldg(root + v), bs[k], nb, depth, prog);
     } else {
       for (int w = 0; w < 8; ++w) X[8 * k + w] = 0u;
     }
   }
-  team_bar(tm.bar, tm.nthr);
+  // with at most one unfixed candidate there is nothing to rank: the network
+  // is not run (the choice is the same), which is common near the leaves
+  const int holders = team_bar_popc(tm.bar, tm.nthr, n_open > 0);
+  if (holders <= 1 && !team_bar_or(tm.bar, tm.nthr, n_open > 1)) {
+    if (n_open == 1) atomicMin(sel, static_cast<unsigned long long>(last));
+    return;
+  }
   for (int c = tm.warp; c < nbp / 16; c += tm.nwarps) {
     float lo, hi;
     mlp_score_chunk(pol, X, c, &lo, &hi);

@@ -42,6 +42,9 @@ def test_scores_match_pytorch_reference():
 
 
 def test_features_match_numpy_restatement():
+    """Every feature against its definition on the scheduling instance
+    itself (degrees, offsets, demand = sum over resources of usage /
+    capacity), not on the packed rows."""
     inst = config_instance("j30", 2)
     rows = pccp.rcpsp.build_rows(inst)
     m = pccp.Model.from_rows(rows)
@@ -64,6 +67,9 @@ def test_features_match_numpy_restatement():
     for (b, x, y, d) in rows["reified"]:
         n_rf[x] += 1
         n_rf[y] += 1
+    # demand of task k: its usages over the capacities, summed over resources
+    demand = np.array([sum(inst.usage[r][k] / inst.capacity[r] for r in range(inst.n_resources))
+                       for k in range(n)])
     lb0, ub0 = rows["lb0"], rows["ub0"]
     for s in range(len(nodes)):
         for k in range(n):
@@ -73,7 +79,8 @@ def test_features_match_numpy_restatement():
             prog = np.float32(max(lb[s, M], lb0[M]) - lb0[M]) / np.float32(ub0[M] - lb0[M] + 1)
             ref = [np.float32(l - lb0[k]) * inv, np.float32(u - lb0[k]) * inv,
                    np.float32(u - l) * inv, np.log2(np.float32(1 + u - l)) / 16,
-                   out_deg[k] / 8, sum_d[k] * inv, in_deg[k] / 8, n_rf[k] / 64, 0.0,
+                   out_deg[k] / 8, sum_d[k] * inv, in_deg[k] / 8, n_rf[k] / 64,
+                   demand[k] / 4,
                    k / n, depth[s] / (depth[s] + 32.0), prog]
             refb = bf(np.array(ref, dtype=np.float32)).numpy()
             assert np.allclose(f[s, k], refb, rtol=2 ** -7, atol=1e-6), (s, k, f[s, k], refb)
@@ -92,9 +99,10 @@ def _random_groups(seed, n_groups=48):
 
 
 def test_first_training_step_follows_autograd():
-    """Adam's first step moves each weight by about -lr * sign(gradient); the
-    gradient of the mean listwise cross-entropy comes from PyTorch autograd on
-    the same BF16-rounded forward (rounding passed straight through)."""
+    """The gradient of the mean listwise cross-entropy equals PyTorch
+    autograd's on the same BF16-rounded forward (rounding passed straight
+    through), element by element; and Adam's first step moves each weight by
+    about -lr * sign(gradient)."""
     pol = pccp.Policy.random(11)
     w0 = pol.weights()
     x, off, t = _random_groups(5)
@@ -116,6 +124,17 @@ def test_first_training_step_follows_autograd():
     L = L / (len(off) - 1)
     L.backward()
     assert abs(loss - L.item()) < 1e-2 * max(1.0, abs(L.item()))
+    # the raw gradient, element by element: the kernels feed BF16 copies of
+    # the activations and of dZ into the tensor-core GEMMs (FP32 accumulate),
+    # so each entry may differ by a few BF16 roundings of the largest terms
+    got = pol.gradients()
+    for k in ("w1", "b1", "w2", "b2", "w3"):
+        gr = P[k].grad.numpy()
+        tol = 2e-2 * np.abs(gr).max() + 1e-6
+        err = np.abs(got[k] - gr)
+        assert err.max() <= tol, (k, float(err.max()), float(tol))
+        assert np.corrcoef(got[k].ravel(), gr.ravel())[0, 1] > 0.999, k
+    assert abs(got["b3"] - float(b3.grad)) <= 2e-2 * abs(float(b3.grad)) + 1e-6
     for k in ("w1", "b1", "w2", "b2", "w3"):
         gr = P[k].grad.numpy()
         upd = w1[k] - w0[k]
@@ -189,3 +208,28 @@ def test_pipeline_collects_and_trains():
     acc1 = learn.ranking_accuracy(pol, data)
     assert losses[-1] - ent < 0.8 * (losses[0] - ent)
     assert acc1 > acc0
+
+
+def test_rollout_labels_are_oracle_proof_sizes():
+    """The rollout labels of learn.collect_rollouts: every child subproblem's
+    node count is the size of its first-fail proof tree (objective bounded
+    below the optimum, so no solution and an order-free count), equal to the
+    oracle's on the same child box; targets are distributions over each
+    node's candidates."""
+    insts = [config_instance("mixed6_10", 5000 + s) for s in range(4)]
+    rec = []
+    data, stats = learn.collect_rollouts(insts, nodes_per_model=3, seed=2, node_cap=10 ** 8,
+                                         record=rec)
+    assert stats["groups"] > 0 and stats["children_capped"] == 0 and len(rec) == stats["children"]
+    off = data["group_off"].cpu().numpy()
+    t = data["target"].cpu().numpy()
+    for a, b in zip(off[:-1], off[1:]):
+        assert b - a >= 2 and abs(t[a:b].sum() - 1) < 1e-4
+    small = [r for r in rec if r[3] <= 20000][:60]  # the oracle re-proves these on the CPU
+    assert len(small) >= 20
+    for inst, lb0, ub0, nodes, status in small:
+        om = rcpsp_model(inst)
+        child = oracle.Model(lb0, ub0, om.temporal, om.linear, om.reified, om.objective, om.branch)
+        o = oracle.solve(child, strategy=oracle.FIRST_FAIL)
+        assert o["status"] == oracle.RES_INFEASIBLE
+        assert nodes == o["nodes"] and status == pccp.PCCP_RES_INFEASIBLE
