@@ -358,6 +358,19 @@ def complete_batch_bench(pccp, policy=None, training=None):
         optima = obj
     out["optima_sum"] = sum(optima)
     if policy is not None:
+        # a second sample of the same family (seeds 7000-7255, disjoint from
+        # the training seeds too): first-fail's proof sizes have a heavy tail,
+        # so the two samples differ
+        held = [pccp.Model.from_rcpsp(config_instance(COMPLETE_FAMILY, s))
+                for s in range(7000, 7000 + COMPLETE_MODELS)]
+        hk = dict(deterministic=False, teams_per_cta=teams, threads=threads)
+        h_ff = pccp.solve_batch(held, strategy=pccp.PCCP_FIRST_FAIL, **hk)
+        h_ln = pccp.solve_batch(held, strategy=pccp.PCCP_LEARNED, policy=policy, **hk)
+        assert [r["objective"] for r in h_ff] == [r["objective"] for r in h_ln]
+        out["held_out_seeds_7000_7255"] = {
+            name: {"ms_to_last_proof": r[0]["elapsed_ms"], "nodes": sum(x["nodes"] for x in r),
+                   "proven": sum(x["status"] == pccp.PCCP_RES_OPTIMAL for x in r)}
+            for name, r in (("first_fail", h_ff), ("learned", h_ln))}
         out["learned_vs_first_fail"] = {
             "time_ratio": out["learned"]["ms_to_last_proof"] / out["first_fail"]["ms_to_last_proof"],
             "node_ratio": out["learned"]["nodes"] / out["first_fail"]["nodes"],

@@ -1041,7 +1041,7 @@ size_t plan_solve_smem(uint32_t max_img, int max_track_words, int max_vars, int 
 
 // Words of shared memory for the learned strategy's feature rows (0 otherwise).
 int policy_x_words(const pccp_solve_opts* o, int max_branch) {
-  return o->strategy == PCCP_LEARNED ? 8 * ((max_branch + 15) & ~15) : 0;
+  return o->strategy == PCCP_LEARNED ? 24 * ((max_branch + 15) & ~15) : 0;
 }
 
 // skip_stable of the launch options: 1 on, -1 off, 0 the library's choice --
@@ -1280,7 +1280,7 @@ int plan_batch(const pccp_model* const* models, int32_t n, const pccp_solve_opts
   if (o->threads < 0 || o->threads % 32 != 0 || o->threads > 1024) return PCCP_ERR_INVALID;
   if (o->teams_per_cta < 0 || o->teams_per_cta > kMaxTeamsPerCta) return PCCP_ERR_INVALID;
   if (o->props_per_thread < 0) return PCCP_ERR_INVALID;
-  p->xw = any_strategy ? 8 * ((max_branch + 15) & ~15) : policy_x_words(o, max_branch);
+  p->xw = any_strategy ? 24 * ((max_branch + 15) & ~15) : policy_x_words(o, max_branch);
   p->max_tw = max_tw;
   p->max_vars = max_vars;
   p->max_depth = max_dec;
@@ -2037,7 +2037,7 @@ int plan_queue(const pccp_model* const* models, int32_t n, const pccp_solve_opts
     max_rows = std::max(max_rows, m->n_t + m->n_rf + m->n_lin);
     max_dec = std::max(max_dec, m->max_decisions);
   }
-  p->xw = any_strategy ? 8 * ((max_branch + 15) & ~15) : policy_x_words(o, max_branch);
+  p->xw = any_strategy ? 24 * ((max_branch + 15) & ~15) : policy_x_words(o, max_branch);
   p->max_len = max_dec;
   p->off_track = static_cast<uint32_t>(align16(16 + sizeof(QCtrl)));
   p->off_x = p->off_track + 4u * static_cast<uint32_t>((max_tw + 3) & ~3);

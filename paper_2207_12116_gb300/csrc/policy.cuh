@@ -91,13 +91,17 @@ __device__ __forceinline__ void write_features(uint32_t* row, int k, int2 D, int
   row[7] = 0u;
 }
 
-// Scores of rows 16c .. 16c+15 of X by one warp.  On return the lanes with
-// (lane & 3) == 0 hold the scores of rows 16c + lane/4 (s_lo) and
-// 16c + lane/4 + 8 (s_hi).  Kept out of line so its 40-odd live registers do
-// not raise the register count of the propagation loop.
-__device__ __noinline__ void mlp_score_chunk(const PolicyDev* __restrict__ pol,
-                                             const uint32_t* X, int c, float* s_lo,
-                                             float* s_hi) {
+// Layer 1 of rows 16c .. 16c+15 of X, then the output tiles j0 .. j1-1 of
+// layer 2 (8 hidden units each) folded into the output weights: for every
+// row and tile, part[16 j + row] = sum over the tile's 8 units of
+// relu(h2 + b2) * w3 (two units per lane, then the 4 lanes of a row).  One
+// warp; the rows' scores are the tiles' parts summed in tile order
+// (mlp_row_score), so the result does not depend on how many warps shared
+// the tiles.  Kept out of line so its 40-odd live registers do not raise
+// the register count of the propagation loop.
+__device__ __noinline__ void mlp_score_tiles(const PolicyDev* __restrict__ pol,
+                                             const uint32_t* X, int c, int j0, int j1,
+                                             float* part) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   const int r0 = 16 * c + g, r1 = r0 + 8;
@@ -116,25 +120,34 @@ __device__ __noinline__ void mlp_score_chunk(const PolicyDev* __restrict__ pol,
     a2[kk][2] = pack_bf16x2(fmaxf(d1[0] + b10, 0.f), fmaxf(d1[1] + b11, 0.f));
     a2[kk][3] = pack_bf16x2(fmaxf(d1[2] + b10, 0.f), fmaxf(d1[3] + b11, 0.f));
   }
-  float p_lo = 0.f, p_hi = 0.f;
 #pragma unroll 1
-  for (int j = 0; j < 16; ++j) {
+  for (int j = j0; j < j1; ++j) {
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) mma_16816(acc, a2[kk], __ldg(&pol->w2[kk][j][lane]));
     const int c0 = 8 * j + 2 * t;
     const float bb0 = __ldg(&pol->b2[c0]), bb1 = __ldg(&pol->b2[c0 + 1]);
     const float w0 = __ldg(&pol->w3[c0]), w1 = __ldg(&pol->w3[c0 + 1]);
-    p_lo += fmaxf(acc[0] + bb0, 0.f) * w0 + fmaxf(acc[1] + bb1, 0.f) * w1;
-    p_hi += fmaxf(acc[2] + bb0, 0.f) * w0 + fmaxf(acc[3] + bb1, 0.f) * w1;
+    float p_lo = fmaxf(acc[0] + bb0, 0.f) * w0 + fmaxf(acc[1] + bb1, 0.f) * w1;
+    float p_hi = fmaxf(acc[2] + bb0, 0.f) * w0 + fmaxf(acc[3] + bb1, 0.f) * w1;
+    p_lo += __shfl_xor_sync(0xffffffffu, p_lo, 1);
+    p_lo += __shfl_xor_sync(0xffffffffu, p_lo, 2);
+    p_hi += __shfl_xor_sync(0xffffffffu, p_hi, 1);
+    p_hi += __shfl_xor_sync(0xffffffffu, p_hi, 2);
+    if (t == 0) {
+      part[16 * j + g] = p_lo;
+      part[16 * j + g + 8] = p_hi;
+    }
   }
-  p_lo += __shfl_xor_sync(0xffffffffu, p_lo, 1);
-  p_lo += __shfl_xor_sync(0xffffffffu, p_lo, 2);
-  p_hi += __shfl_xor_sync(0xffffffffu, p_hi, 1);
-  p_hi += __shfl_xor_sync(0xffffffffu, p_hi, 2);
-  const float b3 = __ldg(&pol->b3);
-  *s_lo = p_lo + b3;
-  *s_hi = p_hi + b3;
+}
+
+// Score of row `row` (0..15) of a chunk from its 16 tile parts, in tile order.
+__device__ __forceinline__ float mlp_row_score(const PolicyDev* __restrict__ pol,
+                                               const float* part, int row) {
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) s += part[16 * j + row];
+  return s + __ldg(&pol->b3);
 }
 
 // Order-preserving map of a float score to an unsigned integer.
@@ -152,9 +165,12 @@ __device__ __forceinline__ unsigned long long learned_key(float s, int k) {
 
 // Learned selection by a whole team after a fixed point: features of every
 // branch variable into X (shared memory, 8 words per row, rows padded to a
-// multiple of 16), a team barrier, then warps score 16-row chunks and submit
-// the unfixed candidates' keys to *sel in the minimum form of the plain
-// strategies (~learned_key: its low 32 bits are the branch index).
+// multiple of 16; then 256 floats of tile parts per 16-row chunk), a team
+// barrier, the warps compute the tile parts of the chunks, a team barrier,
+// and the threads sum the parts of the unfixed candidates and submit their
+// keys to *sel in the minimum form of the plain strategies (~learned_key:
+// its low 32 bits are the branch index).  Words of X per team:
+// policy_x_words = 24 * (branch variables rounded up to 16).
 __device__ __forceinline__ void learned_select(const Tab& tb, int2* st,
                                                const int2* __restrict__ root, const Team& tm,
                                                const PolicyDev* __restrict__ pol, uint32_t* X,
@@ -188,21 +204,20 @@ __device__ __forceinline__ void learned_select(const Tab& tb, int2* st,
     if (n_open == 1) atomicMin(sel, static_cast<unsigned long long>(last));
     return;
   }
-  for (int c = tm.warp; c < nbp / 16; c += tm.nwarps) {
-    float lo, hi;
-    mlp_score_chunk(pol, X, c, &lo, &hi);
-    if ((tm.lane & 3) == 0) {
-      const int r0 = 16 * c + (tm.lane >> 2);
-      const int r1 = r0 + 8;
-      if (r0 < nb) {
-        const int2 D = ld_dom(st, tb.branch[r0]);
-        if (D.x < D.y) atomicMin(sel, ~learned_key(lo, r0));
-      }
-      if (r1 < nb) {
-        const int2 D = ld_dom(st, tb.branch[r1]);
-        if (D.x < D.y) atomicMin(sel, ~learned_key(hi, r1));
-      }
-    }
+  // the 16 output tiles of every 16-row chunk, split across the team's warps
+  // (S warps per chunk when there are enough); parts after the features in X
+  const int n_chunks = nbp / 16;
+  int S = 1;
+  while (S < 16 && n_chunks * S * 2 <= tm.nwarps) S *= 2;
+  float* P = reinterpret_cast<float*>(X + 8 * nbp);  // [n_chunks][16 tiles][16 rows]
+  for (int u = tm.warp; u < n_chunks * S; u += tm.nwarps) {
+    const int c = u / S, sp = u % S;
+    mlp_score_tiles(pol, X, c, sp * (16 / S), (sp + 1) * (16 / S), P + 256 * c);
+  }
+  team_bar(tm.bar, tm.nthr);
+  for (int k = tm.tid; k < nb; k += tm.nthr) {
+    const int2 D = ld_dom(st, tb.branch[k]);
+    if (D.x < D.y) atomicMin(sel, ~learned_key(mlp_row_score(pol, P + 256 * (k >> 4), k & 15), k));
   }
 }
 

@@ -245,6 +245,7 @@ __global__ void k_policy_features(const uint8_t* __restrict__ image, const int2*
 __global__ void k_policy_score(const PolicyDev* __restrict__ pol, int n,
                                const float* __restrict__ f, float* __restrict__ s) {
   __shared__ uint32_t X[8][16 * 8];  // 8 warps x 16 rows x 8 words
+  __shared__ float part[8][256];     // tile parts (mlp_score_tiles)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * 8 + warp;
   uint32_t* Xw = X[warp];
@@ -258,13 +259,9 @@ __global__ void k_policy_score(const PolicyDev* __restrict__ pol, int n,
   }
   __syncwarp();
   if (16 * c >= n) return;
-  float lo, hi;
-  mlp_score_chunk(pol, Xw, 0, &lo, &hi);
-  if ((lane & 3) == 0) {
-    const int r0 = 16 * c + (lane >> 2), r1 = r0 + 8;
-    if (r0 < n) s[r0] = lo;
-    if (r1 < n) s[r1] = hi;
-  }
+  mlp_score_tiles(pol, Xw, 0, 0, 16, part[warp]);
+  __syncwarp();
+  if (lane < 16 && 16 * c + lane < n) s[16 * c + lane] = mlp_row_score(pol, part[warp], lane);
 }
 
 }  // namespace pccp
