@@ -91,6 +91,13 @@ typedef struct {
   int32_t objective;
   int32_t n_branch;
   const int32_t* branch_vars; /* [n_branch] */
+  int32_t bool_store;  /* how the stores keep Boolean variables that appear only as
+                          reified b's and in all-positive 0/1 linear rows: 1 as
+                          bits (two bits of a shared 64-bit word each, 32 x
+                          smaller stores; the table is then read from global
+                          memory), -1 as intervals, 0 the library's choice (bits
+                          only when an interval store would not fit in shared
+                          memory).  Results are the same. */
 } pccp_model_desc;
 
 typedef struct pccp_model pccp_model; /* opaque; owns a device copy of the table */
@@ -125,6 +132,9 @@ typedef struct {
   int32_t reordered;        /* 1: the library keeps the variables in shared memory in
                                its own order (chosen at create for fewer bank conflicts;
                                every array the caller sees stays in the caller's order) */
+  int32_t bool_vars;        /* Booleans kept as bits (see pccp_model_desc.bool_store) */
+  int32_t store_bytes;      /* shared memory of one store: 8 B per other variable and
+                               8 B per 32 Booleans kept as bits */
 } pccp_model_info;
 
 int pccp_model_get_info(const pccp_model* model, pccp_model_info* info);

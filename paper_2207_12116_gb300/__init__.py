@@ -153,7 +153,9 @@ class Model:
     """A created pccp_model (device copy of the packed propagator table)."""
 
     def __init__(self, lb0, ub0, temporal=None, linear_c=None, linear_off=None, term_coef=None,
-                 term_var=None, reified=None, objective=-1, branch=None):
+                 term_var=None, reified=None, objective=-1, branch=None, bool_store=0):
+        """bool_store: 1 keep the Booleans that allow it as bits, -1 as
+        intervals, 0 the library's choice (pccp_model_desc.bool_store)."""
         self.lb0 = _i32(lb0)
         self.ub0 = _i32(ub0)
         self.n_vars = len(self.lb0)
@@ -171,7 +173,7 @@ class Model:
             len(self.linear_c), _ptr(self.linear_c), _ptr(self.linear_off),
             _ptr(self.term_coef), _ptr(self.term_var),
             len(self.reified), _ptr(self.reified),
-            self.objective, len(self.branch), _ptr(self.branch))
+            self.objective, len(self.branch), _ptr(self.branch), int(bool_store))
         rc, h = pccp_model_create(desc)
         check(rc, "pccp_model_create")
         self.handle = h
@@ -180,17 +182,18 @@ class Model:
         self.info = info
 
     @classmethod
-    def from_rows(cls, rows):
+    def from_rows(cls, rows, bool_store=0):
         return cls(rows["lb0"], rows["ub0"], rows["temporal"], rows["linear_c"],
                    rows["linear_off"], rows["term_coef"], rows["term_var"], rows["reified"],
-                   rows["objective"], rows["branch"])
+                   rows["objective"], rows["branch"], bool_store)
 
     @classmethod
-    def from_rcpsp(cls, inst):
-        return cls.from_rows(rcpsp.build_rows(inst))
+    def from_rcpsp(cls, inst, bool_store=0):
+        return cls.from_rows(rcpsp.build_rows(inst), bool_store)
 
     @classmethod
-    def from_lists(cls, lb0, ub0, temporal=(), linear=(), reified=(), objective=-1, branch=()):
+    def from_lists(cls, lb0, ub0, temporal=(), linear=(), reified=(), objective=-1, branch=(),
+                   bool_store=0):
         """temporal [(x, y, d)], linear [(c, [(coef, var), ...])], reified [(b, x, y, d)]."""
         off = [0]
         coef, var = [], []
@@ -200,7 +203,8 @@ class Model:
                 var.append(v)
             off.append(len(coef))
         return cls(lb0, ub0, list(temporal) or np.zeros((0, 3)), [c for c, _ in linear], off,
-                   coef, var, list(reified) or np.zeros((0, 4)), objective, list(branch))
+                   coef, var, list(reified) or np.zeros((0, 4)), objective, list(branch),
+                   bool_store)
 
     @property
     def rows(self) -> int:

@@ -41,13 +41,15 @@ class pccp_model_desc(ctypes.Structure):
         ("n_linear", I32), ("linear_c", P), ("linear_off", P), ("term_coef", P), ("term_var", P),
         ("n_reified", I32), ("reified", P),
         ("objective", I32), ("n_branch", I32), ("branch_vars", P),
+        ("bool_store", I32),
     ]
 
 
 class pccp_model_info(ctypes.Structure):
     _fields_ = [("n_vars", I32), ("n_temporal", I32), ("n_linear", I32), ("n_terms", I32),
                 ("n_reified", I32), ("table_bytes", I32), ("bytes_per_sweep", I64),
-                ("max_store_vars", I32), ("n_segments", I32), ("reordered", I32)]
+                ("max_store_vars", I32), ("n_segments", I32), ("reordered", I32),
+                ("bool_vars", I32), ("store_bytes", I32)]
 
 
 class pccp_launch_config(ctypes.Structure):

@@ -23,6 +23,7 @@ struct PropArgs {
   int* counter;
   uint32_t image_bytes;
   int n_vars;
+  int n_slots;  // store slots per team (variables below bit0, then Boolean words)
   int n_stores;
   int team_size;
   int teams;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   tm.warp = tm.tid >> 5;
   tm.nwarps = a.team_size >> 5;
   PropCtrl* ctrl = ctrl_base + team_id;
-  int2* st = st_base + static_cast<size_t>(team_id) * a.n_vars;
+  int2* st = st_base + static_cast<size_t>(team_id) * a.n_slots;
   const Tab tb = make_tab(kGlobal ? a.image : img);
   const Track tk = make_track(track_base + static_cast<size_t>(tw16) * team_id, tb.n_vars,
                               tb.n_lin + tb.n_lin_long);
@@ -105,12 +106,32 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
     int32_t* lbs = a.lb + static_cast<size_t>(s) * nv;
     int32_t* ubs = a.ub + static_cast<size_t>(s) * nv;
     bool empty = false;
+    const int b0 = tb.bit0;
     for (int x = tm.tid; x < nv; x += tm.nthr) {
       const int v = a.reordered ? __ldg(internal_of + x) : x;
+      if (v >= b0) continue;  // a Boolean kept as a bit: staged below
       const int2 r = __ldg(a.root + v);
       const int l = max(lbs[x], r.x), u = min(ubs[x], r.y);
       st[v] = make_int2(l, u);
       empty |= l > u;
+    }
+    // Booleans kept as bits: a warp per slot of 32, lane j the library's
+    // variable bit0 + 32 slot + j; the slot's two words come from ballots (an
+    // empty input interval leaves its bit empty: lower set, upper clear)
+    for (int wi = tm.warp; b0 + wi < tb.n_slots; wi += tm.nwarps) {
+      const int v = b0 + 32 * wi + tm.lane;
+      bool lbit = false, ubit = true;
+      if (v < nv) {
+        const int x = __ldg(internal_of + nv + v);  // the caller's index (user_of)
+        const int2 r = __ldg(a.root + v);
+        const int l = max(lbs[x], r.x), u = min(ubs[x], r.y);
+        lbit = l > u || l >= 1;
+        ubit = l <= u && u >= 1;
+        empty |= l > u;
+      }
+      const uint32_t lw = __ballot_sync(0xffffffffu, lbit);
+      const uint32_t uw = __ballot_sync(0xffffffffu, ubit);
+      if (tm.lane == 0) st[b0 + wi] = make_int2(static_cast<int>(lw), static_cast<int>(uw));
     }
     if (kTrack) track_clear02(tk, tm);
     if (tm.tid == 0) {
@@ -124,7 +145,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
       status = team_fixpoint<kTrack, kGlobal, kStream>(tb, st, tm, &ctrl->fc, tk, true,
                                                        a.max_iter, it, &stream);
     for (int x = tm.tid; x < nv; x += tm.nthr) {
-      const int2 D = st[a.reordered ? __ldg(internal_of + x) : x];
+      const int2 D = var_dom_plain(st, b0, a.reordered ? __ldg(internal_of + x) : x);
       lbs[x] = D.x;
       ubs[x] = D.y;
     }

@@ -43,6 +43,7 @@ struct EpsArgs {
   int* out_count;
   uint32_t image_bytes;
   int n_vars;
+  int n_slots;           // store slots (variables below bit0, then Boolean words)
   int max_iter;
   int teams;             // per CTA
   int team_size;
@@ -189,14 +190,18 @@ __device__ __forceinline__ void eps_solution(const Tab& tb, int2* st, const Team
     // in the caller's variable order (internal_of after the root)
     int32_t* w = a.witness + static_cast<size_t>(team_gid) * a.n_vars;
     const int32_t* internal_of = reinterpret_cast<const int32_t*>(a.root + a.n_vars);
-    for (int x = tm.tid; x < a.n_vars; x += tm.nthr) w[x] = st[__ldg(internal_of + x)].x;
+    for (int x = tm.tid; x < a.n_vars; x += tm.nthr)
+      w[x] = var_dom_plain(st, tb.bit0, __ldg(internal_of + x)).x;
   }
 }
 
 template <bool kTrack>
 __device__ __forceinline__ void eps_restore(const int2* root, int2* st, const Team& tm, int nv,
-                                            const Track& tk, const int2* path, int len) {
-  for (int v = tm.tid; v < nv; v += tm.nthr) st[v] = __ldg(root + v);
+                                            int n_slots, const Track& tk, const int2* path,
+                                            int len) {
+  // the root in the store layout follows the root box and the two index maps
+  const int2* root_store = root + 2 * static_cast<size_t>(nv);
+  for (int v = tm.tid; v < n_slots; v += tm.nthr) st[v] = __ldg(root_store + v);
   if (kTrack) track_clear02(tk, tm);
   team_bar(tm.bar, tm.nthr);
   for (int k = tm.tid; k < len; k += tm.nthr) {
@@ -248,8 +253,8 @@ __device__ __forceinline__ EpsSmem eps_smem(uint8_t* smem, const EpsArgs& a, int
       reinterpret_cast<uint32_t*>(smem + img_bytes + 16 + sizeof(EpsCtrl) * a.teams);
   s.track = track_base + static_cast<size_t>(tw16) * team_id;
   int2* st_base = reinterpret_cast<int2*>(track_base + static_cast<size_t>(tw16) * a.teams);
-  s.st = st_base + static_cast<size_t>(team_id) * a.n_vars;
-  uint32_t* x_base = reinterpret_cast<uint32_t*>(st_base + static_cast<size_t>(a.teams) * a.n_vars);
+  s.st = st_base + static_cast<size_t>(team_id) * a.n_slots;
+  uint32_t* x_base = reinterpret_cast<uint32_t*>(st_base + static_cast<size_t>(a.teams) * a.n_slots);
   s.X = x_base + static_cast<size_t>(team_id) * a.x_words;
   return s;
 }
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
     const int p = sc->next;
     if (p >= a.n_in) break;
     const int2* path = a.in_paths + static_cast<size_t>(p) * a.in_len;
-    eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, tk, path, a.in_len);
+    eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, a.n_slots, tk, path, a.in_len);
     int it = 0;
     unsigned long long key = 0;
     const int r = eps_node<kTrack, kLearned, kGlobal, kStream>(tb, sm.st, tm, sc, tk, false, par, a, it,
@@ -400,7 +405,7 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
     const int2* path = a.in_paths + static_cast<size_t>(p) * base;
     for (int k = tm.tid; k < base; k += tm.nthr) stack[k] = path[k];
     int depth = base;  // thread 0's copy is authoritative
-    eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, tk, path, base);
+    eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, a.n_slots, tk, path, base);
     bool seeded = false;  // team-uniform
     for (;;) {
       int it = 0;
@@ -468,7 +473,7 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
       team_bar(tm.bar, tm.nthr);
       const int d = sc->depth;
       if (d < 0) break;  // subtree exhausted: next subproblem
-      eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, tk, stack, d);
+      eps_restore<kTrack>(a.root, sm.st, tm, a.n_vars, a.n_slots, tk, stack, d);
       seeded = false;
     }
   }

@@ -38,6 +38,9 @@ namespace {
 constexpr int kDefaultMaxIter = 1 << 24;
 constexpr int kMaxTeamsPerCta = 15;  // named barriers 1..15
 constexpr int32_t kValueLimit = (1 << 30) - 1;
+// shared memory a store needs beside its interval slots (control, change
+// words): an interval store within this of the limit keeps Booleans as bits
+constexpr int64_t kBitStoreSlack = 8192;
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
@@ -140,6 +143,8 @@ __device__ __noinline__ void team_dfs(const Tab& tb, const int2* __restrict__ ro
                          int max_iter, int32_t* witness, InstanceResult* out, uint32_t* X,
                          Streamer* stream) {
   const int nv = tb.n_vars;
+  // the root in the store layout (after the root box and the two index maps)
+  const int2* root_store = root + 2 * static_cast<size_t>(nv);
   // thread 0's state (only thread 0 reads or writes it)
   auto& S = sc->ds;
   if (tm.tid == 0) {
@@ -153,7 +158,7 @@ __device__ __noinline__ void team_dfs(const Tab& tb, const int2* __restrict__ ro
   // (left descent) rather than a store built from the root
   bool seeded = false;
 
-  for (int v = tm.tid; v < nv; v += tm.nthr) st[v] = __ldg(root + v);
+  for (int v = tm.tid; v < tb.n_slots; v += tm.nthr) st[v] = __ldg(root_store + v);
   if (kTrack) track_clear02(tk, tm);
 
   for (;;) {
@@ -238,7 +243,8 @@ __device__ __noinline__ void team_dfs(const Tab& tb, const int2* __restrict__ ro
         team_bar(tm.bar, tm.nthr);  // N3
         if (sc->record) {  // in the caller's variable order (internal_of after the root)
           const int32_t* internal_of = reinterpret_cast<const int32_t*>(root + nv);
-          for (int x = tm.tid; x < nv; x += tm.nthr) witness[x] = st[__ldg(internal_of + x)].x;
+          for (int x = tm.tid; x < nv; x += tm.nthr)
+            witness[x] = var_dom_plain(st, tb.bit0, __ldg(internal_of + x)).x;
         }
       } else {
         backtrack = false;
@@ -280,7 +286,7 @@ __device__ __noinline__ void team_dfs(const Tab& tb, const int2* __restrict__ ro
       team_bar(tm.bar, tm.nthr);  // N4
       const int d = sc->depth;
       if (d < 0) break;
-      for (int v = tm.tid; v < nv; v += tm.nthr) st[v] = __ldg(root + v);
+      for (int v = tm.tid; v < tb.n_slots; v += tm.nthr) st[v] = __ldg(root_store + v);
       if (kTrack) track_clear02(tk, tm);
       seeded = false;
       team_bar(tm.bar, tm.nthr);  // N5
@@ -439,10 +445,12 @@ __global__ void __launch_bounds__(1024) k_solve_slots(SolveArgs a) {
     const TableHeader* hg = reinterpret_cast<const TableHeader*>(d.image);
     // the image prefix after the store, 128-byte aligned, when it fits
     const uint32_t img_off =
-        (a.off_store + 8u * static_cast<uint32_t>(d.n_vars) + 127u) & ~127u;
+        (a.off_store + 8u * static_cast<uint32_t>(__ldg(&hg->n_slots)) + 127u) & ~127u;
     const uint32_t copy = static_cast<uint32_t>(kTrackS ? __ldg(&hg->track_bytes)
                                                         : __ldg(&hg->core_bytes));
-    if (img_off + copy <= a.slot_bytes) {
+    // models keeping Booleans as bits are read in place (only the
+    // global-table instantiations read that layout)
+    if (img_off + copy <= a.slot_bytes && __ldg(&hg->bit0) == d.n_vars) {
       uint8_t* img = slot + img_off;
       if (!team_load_image(img, d.image, copy, mbar, parity, tm)) {
         if (tm.tid == 0) {
@@ -475,6 +483,7 @@ struct Packed {
   int32_t n_seg;
   int64_t bytes_per_sweep;
   uint32_t core_bytes, track_bytes;  // image prefixes copied to shared memory
+  int32_t bit0, n_slots;             // store layout
 };
 
 size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
@@ -500,6 +509,7 @@ struct pccp_model {
   int64_t bytes_per_sweep;
   int32_t max_iter;  // every changing iteration narrows some bound by >= 1
   int32_t max_decisions;  // bound on a search path's length (decision stack entries)
+  int32_t bit0, n_slots;  // store layout: Booleans from bit0 on as bits; int2 slots per store
   uint8_t* d_mem;    // image, then root int2[n_vars]
   int2* d_root;
   HostPipe* pipe = nullptr;  // pccp_propagate_host's streams and slots (lazy)
@@ -628,6 +638,106 @@ int64_t sweep_wavefronts(const pccp_model_desc* d, const std::vector<uint2>& RF,
 // (sweep_wavefronts) is kept.  The caller's order stays the interface:
 // stores are read and written, and witnesses written, through this map.
 // Identity when the model has an index out of range (validation reports it).
+// Booleans that may be kept as bits (2 bits of a shared 64-bit slot instead
+// of an int2 each): variables with a 0/1 root domain that appear only as the
+// b of reified rows and as terms of linear rows whose coefficients are all
+// positive and whose variables are all 0/1 at the root (the overlap Booleans
+// and resource sums of the scheduling model), never as a branch variable,
+// the objective, or an operand of another row.  Every reified b and every
+// term of such a linear row must then be one of them, else the model keeps
+// every variable as an interval (empty result).  Indices are the caller's.
+std::vector<char> bit_vars(const pccp_model_desc* d) {
+  const int32_t nv = d->n_vars;
+  if (nv <= 0 || nv > 65535 || !d->lb0 || !d->ub0) return {};
+  if (d->n_temporal < 0 || d->n_reified < 0 || d->n_linear < 0 || d->n_branch < 0) return {};
+  if ((d->n_temporal > 0 && !d->temporal) || (d->n_reified > 0 && !d->reified) ||
+      (d->n_branch > 0 && !d->branch_vars))
+    return {};
+  if (d->n_linear > 0 && (!d->linear_c || !d->linear_off || !d->term_var || !d->term_coef ||
+                          d->linear_off[0] != 0))
+    return {};
+  auto ok = [nv](int32_t v) { return v >= 0 && v < nv; };
+  std::vector<char> bit(nv, 0);
+  for (int32_t v = 0; v < nv; ++v) bit[v] = d->lb0[v] >= 0 && d->ub0[v] <= 1 && d->lb0[v] <= d->ub0[v];
+  for (int32_t k = 0; k < d->n_branch; ++k) {
+    if (!ok(d->branch_vars[k])) return {};
+    bit[d->branch_vars[k]] = 0;
+  }
+  if (d->objective >= 0) {
+    if (!ok(d->objective)) return {};
+    bit[d->objective] = 0;
+  }
+  for (int32_t i = 0; i < d->n_temporal; ++i)
+    for (int c = 0; c < 2; ++c) {
+      if (!ok(d->temporal[3 * i + c])) return {};
+      bit[d->temporal[3 * i + c]] = 0;
+    }
+  for (int32_t i = 0; i < d->n_reified; ++i)
+    for (int c = 0; c < 3; ++c)
+      if (!ok(d->reified[4 * i + c])) return {};
+  for (int32_t i = 0; i < d->n_reified; ++i)
+    for (int c = 1; c < 3; ++c) bit[d->reified[4 * i + c]] = 0;
+  std::vector<char> zero_one_row(d->n_linear > 0 ? d->n_linear : 0, 1);
+  for (int32_t i = 0; i < d->n_linear; ++i) {
+    if (d->linear_off[i + 1] < d->linear_off[i]) return {};
+    for (int32_t k = d->linear_off[i]; k < d->linear_off[i + 1]; ++k) {
+      const int32_t v = d->term_var[k], a = d->term_coef[k];
+      if (!ok(v)) return {};
+      if (a == 0) continue;
+      if (a < 0 || d->lb0[v] < 0 || d->ub0[v] > 1) zero_one_row[i] = 0;
+    }
+  }
+  for (int32_t i = 0; i < d->n_linear; ++i)
+    if (!zero_one_row[i])
+      for (int32_t k = d->linear_off[i]; k < d->linear_off[i + 1]; ++k)
+        if (d->term_coef[k] != 0) bit[d->term_var[k]] = 0;
+  for (int32_t i = 0; i < d->n_reified; ++i)
+    if (!bit[d->reified[4 * i]]) return {};
+  for (int32_t i = 0; i < d->n_linear; ++i)
+    if (zero_one_row[i])
+      for (int32_t k = d->linear_off[i]; k < d->linear_off[i + 1]; ++k)
+        if (d->term_coef[k] != 0 && !bit[d->term_var[k]]) return {};
+  return bit;
+}
+
+// Order with Booleans kept as bits: the other variables first (caller's
+// order), then the Booleans: the first Booleans of reified pairs in pair
+// order, then the second ones, then the rest (neighbouring lanes that
+// evaluate neighbouring pairs then read bits of the same slot).
+std::vector<int32_t> bit_order(const pccp_model_desc* d, const std::vector<char>& bit) {
+  const int32_t nv = d->n_vars;
+  std::vector<int32_t> iof(nv);
+  std::vector<uint2> RF;
+  for (int32_t i = 0; i < d->n_reified; ++i)
+    RF.push_back(make_uint2(static_cast<uint32_t>(d->reified[4 * i + 1]) |
+                                (static_cast<uint32_t>(d->reified[4 * i + 2]) << 16),
+                            static_cast<uint32_t>(d->reified[4 * i])));
+  std::stable_sort(RF.begin(), RF.end(),
+                   [](const uint2& p, const uint2& q) { return (p.y & 0xffffu) < (q.y & 0xffffu); });
+  std::vector<int32_t> rank(nv, 2);  // 0 first Booleans, 1 second ones, 2 the rest
+  std::vector<int32_t> first, second;
+  for (const auto& pq : reified_pairs(RF)) {
+    const int32_t b1 = static_cast<int32_t>(RF[pq.first].y & 0xffffu);
+    const int32_t b2 = static_cast<int32_t>(RF[pq.second].y & 0xffffu);
+    if (rank[b1] == 2) {
+      rank[b1] = 0;
+      first.push_back(b1);
+    }
+    if (rank[b2] == 2) {
+      rank[b2] = 1;
+      second.push_back(b2);
+    }
+  }
+  int32_t next = 0;
+  for (int32_t v = 0; v < nv; ++v)
+    if (!bit[v]) iof[v] = next++;
+  for (int32_t v : first) iof[v] = next++;
+  for (int32_t v : second) iof[v] = next++;
+  for (int32_t v = 0; v < nv; ++v)
+    if (bit[v] && rank[v] == 2) iof[v] = next++;
+  return iof;
+}
+
 std::vector<int32_t> internal_order(const pccp_model_desc* d) {
   const int32_t nv = d->n_vars;
   std::vector<int32_t> iof(nv > 0 ? nv : 0);
@@ -674,7 +784,7 @@ std::vector<int32_t> internal_order(const pccp_model_desc* d) {
                                                                                        : iof;
 }
 
-int validate_and_pack(const pccp_model_desc* d, Packed* p) {
+int validate_and_pack(const pccp_model_desc* d, Packed* p, int32_t bit0 = -1) {
   if (!d) return PCCP_ERR_INVALID;
   const int64_t nv = d->n_vars;
   if (nv < 1) return PCCP_ERR_INVALID;
@@ -876,6 +986,9 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   TableHeader h;
   std::memset(&h, 0, sizeof(h));
   h.n_vars = static_cast<int32_t>(nv);
+  // store layout: Booleans from bit0 on kept as bits (bit_vars), 32 a slot
+  h.bit0 = (bit0 >= 0 && bit0 < nv) ? bit0 : static_cast<int32_t>(nv);
+  h.n_slots = h.bit0 + static_cast<int32_t>((nv - h.bit0 + 31) / 32);
   h.n_t = static_cast<int32_t>(T.size());
   h.n_rf = static_cast<int32_t>(RF.size());
   h.n_rfp = static_cast<int32_t>(RFP.size());
@@ -1001,6 +1114,8 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p) {
   p->n_seg = h.n_seg;
   p->core_bytes = static_cast<uint32_t>(h.core_bytes);
   p->track_bytes = static_cast<uint32_t>(h.track_bytes);
+  p->bit0 = h.bit0;
+  p->n_slots = h.n_slots;
   return PCCP_OK;
 }
 
@@ -1147,14 +1262,15 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   int team = (cfg && cfg->team_threads > 0) ? cfg->team_threads : 128;
   if (team % 32 != 0 || team > 1024) return PCCP_ERR_INVALID;
   const size_t per_team = sizeof(PropCtrl) + 4 * ((track_words(m->n_vars, m->n_lin) + 3) & ~3) +
-                          static_cast<size_t>(m->n_vars) * sizeof(int2);
+                          static_cast<size_t>(m->n_slots) * sizeof(int2);
   // the table lives in shared memory when it fits beside one team's store
   // (the prefix the kernel needs: with change tracking, the adjacency too);
   // otherwise every CTA reads it from the device image (through L1 / L2)
   const uint32_t img_smem =
       use_skip_stable(cfg ? cfg->skip_stable : 0, false) ? m->track_bytes : m->core_bytes;
-  const bool global = static_cast<size_t>(img_smem) + 16 + per_team >
-                      static_cast<size_t>(smem_max);
+  const bool bits = m->bit0 < m->n_vars;  // read only by the global-table kernels
+  const bool global = bits || static_cast<size_t>(img_smem) + 16 + per_team >
+                                  static_cast<size_t>(smem_max);
   const size_t base = (global ? 0 : static_cast<size_t>(img_smem)) + 16;
   if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   if (global && !(cfg && cfg->team_threads > 0)) team = 1024;
@@ -1223,6 +1339,7 @@ int launch_propagate(const pccp_model* m, const PropPlan& plan, int32_t n_stores
   a.counter = counter;
   a.image_bytes = plan.table_global ? m->image_bytes : plan.copy_bytes;
   a.n_vars = m->n_vars;
+  a.n_slots = m->n_slots;
   a.n_stores = n_stores;
   a.team_size = plan.team;
   a.teams = plan.teams;
@@ -1251,8 +1368,8 @@ struct BatchPlan {
 // Shared memory a model needs in a slot whose store starts at off_store:
 // the store, then its table prefix 128-byte aligned (when `staged`).
 uint32_t slot_need(const pccp_model* m, uint32_t off_store, bool track, bool staged) {
-  const uint32_t st_end = off_store + 8u * static_cast<uint32_t>(m->n_vars);
-  if (!staged) return st_end;
+  const uint32_t st_end = off_store + 8u * static_cast<uint32_t>(m->n_slots);
+  if (!staged || m->bit0 < m->n_vars) return st_end;  // bit layouts are read in place
   return ((st_end + 127u) & ~127u) + (track ? m->track_bytes : m->core_bytes);
 }
 
@@ -1270,7 +1387,7 @@ int plan_batch(const pccp_model* const* models, int32_t n, const pccp_solve_opts
   for (int32_t i = 0; i < n; ++i) {
     const pccp_model* m = models[i];
     max_dec = std::max(max_dec, m->max_decisions);
-    max_vars = std::max(max_vars, m->n_vars);
+    max_vars = std::max(max_vars, m->n_slots);  // store slots
     max_branch = std::max(max_branch, m->n_branch);
     max_tw = std::max(max_tw, track_words(m->n_vars, m->n_lin));
     max_seg = std::max(max_seg, m->n_seg);
@@ -1465,9 +1582,31 @@ int pccp_model_create(const pccp_model_desc* desc_user, pccp_model** out) {
   if (!out) return PCCP_ERR_INVALID;
   *out = nullptr;
   if (!desc_user) return PCCP_ERR_INVALID;
-  // the model in the library's variable order (internal_order)
-  const std::vector<int32_t> iof = internal_order(desc_user);
   const int32_t nv_user = desc_user->n_vars > 0 ? desc_user->n_vars : 0;
+  // Booleans kept as bits when the model allows it (bit_vars) and either the
+  // caller asks for it or an interval store would exceed kBitStoreMinBytes
+  std::vector<char> bits;
+  int32_t n_bits = 0;
+  if (desc_user->bool_store >= 0) {
+    bits = bit_vars(desc_user);
+    for (char b : bits) n_bits += b ? 1 : 0;
+    // by default only where an interval store could not fit in shared memory
+    // at all (the model would be refused): bits cost an extraction per
+    // Boolean read and are read only by the global-table kernels, which
+    // measured slower than interval stores wherever those fit
+    bool want = desc_user->bool_store > 0;
+    if (!want && n_bits > 0) {
+      const int smem_max = max_dyn_smem();
+      want = smem_max > 0 && 8ll * nv_user + kBitStoreSlack > smem_max;
+    }
+    if (n_bits == 0 || !want) {
+      bits.clear();
+      n_bits = 0;
+    }
+  }
+  // the model in the library's variable order (internal_order / bit_order)
+  const std::vector<int32_t> iof =
+      bits.empty() ? internal_order(desc_user) : bit_order(desc_user, bits);
   std::vector<int32_t> uof(nv_user);
   for (int32_t v = 0; v < nv_user; ++v) uof[iof[v]] = v;
   auto map_var = [&iof, nv_user](int32_t v) { return v >= 0 && v < nv_user ? iof[v] : v; };
@@ -1515,7 +1654,7 @@ int pccp_model_create(const pccp_model_desc* desc_user, pccp_model** out) {
   dd.objective = map_var(desc_user->objective);
   const pccp_model_desc* desc = &dd;
   Packed p;
-  const int rc = validate_and_pack(desc, &p);
+  const int rc = validate_and_pack(desc, &p, n_bits > 0 ? nv_user - n_bits : -1);
   if (rc != PCCP_OK) return rc;
   int dev = 0;
   PCCP_CUDA(cudaGetDevice(&dev));
@@ -1555,10 +1694,29 @@ int pccp_model_create(const pccp_model_desc* desc_user, pccp_model** out) {
     m->max_decisions = static_cast<int32_t>(std::min<int64_t>(dec, INT32_MAX));
   }
   // device memory: image | root int2[n] | internal_of int32[n] | user_of int32[n]
+  // device memory: image | root int2[n] | internal_of int32[n] | user_of
+  // int32[n] | the root in the store layout int2[n_slots] (Boolean slots as
+  // bit words; bits past the last Boolean: lower 0, upper 1)
   const size_t root_off = align16(p.image.size());
-  const size_t total = root_off + static_cast<size_t>(p.n_vars) * (sizeof(int2) + 8);
+  const size_t total = root_off + static_cast<size_t>(p.n_vars) * (sizeof(int2) + 8) +
+                       static_cast<size_t>(p.n_slots) * sizeof(int2);
   std::vector<int2> root(p.n_vars);
   for (int v = 0; v < p.n_vars; ++v) root[v] = make_int2(desc->lb0[v], desc->ub0[v]);
+  std::vector<int2> root_store(p.n_slots);
+  for (int v = 0; v < p.bit0; ++v) root_store[v] = root[v];
+  for (int sl = p.bit0; sl < p.n_slots; ++sl) {
+    uint32_t lw = 0u, uw = 0u;
+    for (int j = 0; j < 32; ++j) {
+      const int v = p.bit0 + 32 * (sl - p.bit0) + j;
+      const bool lbit = v < p.n_vars && root[v].x >= 1;
+      const bool ubit = v >= p.n_vars || root[v].y >= 1;
+      lw |= lbit ? (1u << j) : 0u;
+      uw |= ubit ? (1u << j) : 0u;
+    }
+    root_store[sl] = make_int2(static_cast<int>(lw), static_cast<int>(uw));
+  }
+  m->bit0 = p.bit0;
+  m->n_slots = p.n_slots;
   if (cudaMalloc(&m->d_mem, total) != cudaSuccess) {
     (void)cudaGetLastError();
     delete m;
@@ -1572,7 +1730,9 @@ int pccp_model_create(const pccp_model_desc* desc_user, pccp_model** out) {
       cudaMemcpy(d_iof, iof.data(), iof.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
       cudaMemcpy(d_iof + p.n_vars, uof.data(), uof.size() * sizeof(int32_t),
-                 cudaMemcpyHostToDevice) != cudaSuccess) {
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_root + 2 * static_cast<size_t>(p.n_vars), root_store.data(),
+                 root_store.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
     (void)cudaGetLastError();
     cudaFree(m->d_mem);
     delete m;
@@ -1608,6 +1768,8 @@ int pccp_model_get_info(const pccp_model* m, pccp_model_info* info) {
   info->max_store_vars = room > 0 ? static_cast<int32_t>(std::min<int64_t>(room / 8, 65535)) : 0;
   info->n_segments = m->n_seg;
   info->reordered = m->reordered;
+  info->bool_vars = m->n_vars - m->bit0;
+  info->store_bytes = 8 * m->n_slots;
   return PCCP_OK;
 }
 
@@ -1787,13 +1949,13 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
   if (team % 32 != 0 || team > 1024) return PCCP_ERR_INVALID;
   const int xw = policy_x_words(o, m->n_branch);
   const size_t per_team = sizeof(EpsCtrl) + 4 * ((track_words(m->n_vars, m->n_lin) + 3) & ~3) +
-                          static_cast<size_t>(m->n_vars) * sizeof(int2) +
+                          static_cast<size_t>(m->n_slots) * sizeof(int2) +
                           4 * static_cast<size_t>(xw);
   const uint32_t img_smem =
       (o->strategy != PCCP_LEARNED && use_skip_stable(o->skip_stable, false)) ? m->track_bytes
                                                                               : m->core_bytes;
-  const bool global = static_cast<size_t>(img_smem) + 16 + per_team >
-                      static_cast<size_t>(smem_max);
+  const bool global = m->bit0 < m->n_vars || static_cast<size_t>(img_smem) + 16 + per_team >
+                                                  static_cast<size_t>(smem_max);
   const size_t base = (global ? 0 : static_cast<size_t>(img_smem)) + 16;
   if (base + per_team > static_cast<size_t>(smem_max)) return PCCP_ERR_SMEM;
   if (global && o->threads <= 0) team = 1024;
@@ -1866,6 +2028,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     a.in_counter = reinterpret_cast<int*>(d + o_cnt);
     a.out_count = reinterpret_cast<int*>(d + o_cnt + 4);
     a.n_vars = m->n_vars;
+    a.n_slots = m->n_slots;
     a.max_iter = m->max_iter;
     a.teams = teams;
     a.team_size = team;
@@ -1995,6 +2158,7 @@ namespace {
 struct QueuePlan {
   void (*kern)(QArgs);
   int team, teams, grid, max_len, xw;
+  int mode;  // queue_kernel's mode
   size_t smem;
   uint32_t slot_bytes, off_track, off_x, off_stack, off_store;
   bool shared, table_global;
@@ -2009,9 +2173,12 @@ void (*queue_kernel_t(const pccp_solve_opts* o))(QArgs) {
   return k_search_queue<false, true, false, kMode>;
 }
 // mode 0: a slot per team (many models); 1: one model, table shared in the
-// CTA; 2: one model, table read in place
+// CTA; 2: one model, table read in place; 3: mode 2 with Booleans as bits
 void (*queue_kernel(const pccp_solve_opts* o, int mode))(QArgs) {
-  return mode == 0 ? queue_kernel_t<0>(o) : mode == 1 ? queue_kernel_t<1>(o) : queue_kernel_t<2>(o);
+  return mode == 0   ? queue_kernel_t<0>(o)
+         : mode == 1 ? queue_kernel_t<1>(o)
+         : mode == 2 ? queue_kernel_t<2>(o)
+                     : queue_kernel_t<3>(o);
 }
 
 // Team size of a search when the caller leaves it to the library: enough
@@ -2051,10 +2218,11 @@ int plan_queue(const pccp_model* const* models, int32_t n, const pccp_solve_opts
     // one model: its table once per CTA, shared by the CTA's teams
     const pccp_model* m = models[0];
     const uint32_t per = static_cast<uint32_t>(
-        (p->off_store + 8ull * static_cast<uint32_t>(m->n_vars) + 127u) & ~127ull);
+        (p->off_store + 8ull * static_cast<uint32_t>(m->n_slots) + 127u) & ~127ull);
     const uint32_t img = track_s ? m->track_bytes : m->core_bytes;
     const uint32_t region = ((img + 127u) & ~127u) + 128u;
-    p->table_global = static_cast<size_t>(region) + per > static_cast<size_t>(smem_max);
+    p->table_global = m->bit0 < m->n_vars ||  // bit layouts are read in place
+                      static_cast<size_t>(region) + per > static_cast<size_t>(smem_max);
     if (per > static_cast<uint32_t>(smem_max)) return PCCP_ERR_SMEM;
     p->shared_bytes = p->table_global ? 0u : img;
     p->shared_region = p->table_global ? 0u : region;
@@ -2071,7 +2239,8 @@ int plan_queue(const pccp_model* const* models, int32_t n, const pccp_solve_opts
     p->teams = teams;
     p->slot_bytes = per;
     p->smem = p->shared_region + static_cast<size_t>(teams) * per;
-    p->kern = queue_kernel(o, p->table_global ? 2 : 1);
+    p->mode = !p->table_global ? 1 : models[0]->bit0 < models[0]->n_vars ? 3 : 2;
+    p->kern = queue_kernel(o, p->mode);
   } else {
     // many models: a slot per team, as the batched search plans them
     pccp_solve_opts q = *o;
@@ -2096,13 +2265,14 @@ int plan_queue(const pccp_model* const* models, int32_t n, const pccp_solve_opts
     p->teams = teams;
     p->slot_bytes = (want + 127u) & ~127u;
     p->smem = static_cast<size_t>(teams) * p->slot_bytes;
+    p->mode = 0;
     p->kern = queue_kernel(o, 0);
   }
   void (*kerns[8])(QArgs) = {p->kern};
   int n_kerns = 1;
   if (any_strategy) {  // a batch planned once for every later search
     pccp_solve_opts q = *o;
-    const int mode = p->shared ? (p->table_global ? 2 : 1) : 0;
+    const int mode = p->mode;
     for (int strategy : {PCCP_INPUT_ORDER, PCCP_LEARNED})
       for (int skip : {-1, 0, 1}) {
         q.strategy = strategy;

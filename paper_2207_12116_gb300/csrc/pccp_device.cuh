@@ -19,7 +19,7 @@ namespace pccp {
 
 enum : int { kFixpoint = 0, kFailed = 1, kError = 2 };
 
-// Header at the start of the packed table image (112 bytes).  The image is
+// Header at the start of the packed table image (128 bytes).  The image is
 // copied verbatim into shared memory, so every offset is relative to its start
 // and 16-byte aligned.
 struct TableHeader {
@@ -34,8 +34,13 @@ struct TableHeader {
   // tracking, track_bytes (also the variable -> linear-row adjacency) with it;
   // the stream segment list after them is only read from global memory
   int32_t core_bytes, track_bytes;
+  // store layout: variables 0 .. bit0-1 as int2 {lb, ub} slots; variables
+  // bit0 .. n_vars-1 (Booleans, when the model keeps them as bits) 32 to a
+  // slot {lb bits, ub bits}; n_slots = bit0 + ceil((n_vars - bit0) / 32)
+  int32_t bit0, n_slots;
+  int32_t pad2[2];
 };
-static_assert(sizeof(TableHeader) == 112, "header must be 112 bytes");
+static_assert(sizeof(TableHeader) == 128, "header must be 128 bytes");
 
 // Streamed tables.  When a table does not fit in shared memory beside a store,
 // a sweep brings its rows in as a cyclic sequence of segments of at most
@@ -88,6 +93,7 @@ struct Tab {
   int rows_sweep, bytes_sweep;
   const StreamSeg* seg;
   int n_seg;
+  int bit0, n_slots;  // store layout (see TableHeader)
 };
 
 __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
@@ -117,6 +123,8 @@ __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
   tb.seg = reinterpret_cast<const StreamSeg*>(img + h->off_seg);
   tb.n_seg = h->n_seg;
   tb.rfp = reinterpret_cast<const uint4*>(img + h->off_rfp);
+  tb.bit0 = h->bit0;
+  tb.n_slots = h->n_slots;
   return tb;
 }
 
@@ -153,6 +161,53 @@ __device__ __forceinline__ int atom_min_s32(int* p, int v) {
                : "r"(smem_u32(p)), "r"(v)
                : "memory");
   return old;
+}
+
+// Relaxed CTA-scope shared atomic OR / AND returning the old word (the joins
+// of a slot of Booleans: OR raises lower bounds, AND lowers upper bounds).
+__device__ __forceinline__ uint32_t atom_or_old(int* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.relaxed.cta.shared::cta.or.b32 %0, [%1], %2;"
+               : "=r"(old)
+               : "r"(smem_u32(p)), "r"(v)
+               : "memory");
+  return old;
+}
+
+__device__ __forceinline__ uint32_t atom_and_old(int* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.relaxed.cta.shared::cta.and.b32 %0, [%1], %2;"
+               : "=r"(old)
+               : "r"(smem_u32(p)), "r"(v)
+               : "memory");
+  return old;
+}
+
+// Domain of variable v in a store of either layout: an int2 slot below bit0,
+// else bit (v - bit0) % 32 of slot bit0 + (v - bit0) / 32, lower bounds in the
+// slot's first word and upper bounds in its second (one 8-byte relaxed load
+// either way).
+// kBits = false (kernels for tables staged in shared memory, whose models
+// never keep bits): a plain interval load.
+template <bool kBits = true>
+__device__ __forceinline__ int2 ld_var(const int2* st, int bit0, int v) {
+  if (!kBits || v < bit0) return ld_dom(st, v);
+  const int q = v - bit0;
+  const int2 W = ld_dom(st, bit0 + (q >> 5));
+  return make_int2((W.x >> (q & 31)) & 1, (W.y >> (q & 31)) & 1);
+}
+
+// Value of variable v (its lower bound) for witnesses and write-back.
+__device__ __forceinline__ int2 var_dom_plain(const int2* st, int bit0, int v) {
+  if (v < bit0) return st[v];
+  const int q = v - bit0;
+  const int2 W = st[bit0 + (q >> 5)];
+  return make_int2((W.x >> (q & 31)) & 1, (W.y >> (q & 31)) & 1);
+}
+
+// Emptiness of one store slot (an interval, or 32 Booleans).
+__device__ __forceinline__ bool slot_empty(int2 D, int slot, int bit0) {
+  return slot < bit0 ? D.x > D.y : (static_cast<uint32_t>(D.x) & ~static_cast<uint32_t>(D.y)) != 0u;
 }
 
 __device__ __forceinline__ void st_relaxed(int* p, int v) {
@@ -373,6 +428,50 @@ __device__ __forceinline__ void tell_ub(const Sweep& w, int v, int cand, int lb_
   }
 }
 
+// Tells on a variable that may be a Boolean kept as bits (the b of a
+// reified row, a term of an all-positive 0/1 linear row): candidates are 0 or
+// 1 there, so a tell sets the lower bit (OR) or clears the upper bit (AND);
+// below bit0 they are the interval tells.
+template <bool kTrack, bool kBits>
+__device__ __forceinline__ void tell_lb_v(const Sweep& w, int v, int cand, int lb_seen,
+                                          int ub_seen, Flags& f) {
+  if (!kBits || v < w.tb.bit0) {
+    tell_lb<kTrack>(w, v, cand, lb_seen, ub_seen, f);
+    return;
+  }
+  if (cand <= lb_seen) return;
+  if (cand > ub_seen) {
+    f.fl = true;
+    return;
+  }
+  const int q = v - w.tb.bit0;
+  const uint32_t m = 1u << (q & 31);
+  if (!(atom_or_old(&w.st[w.tb.bit0 + (q >> 5)].x, m) & m)) {
+    f.ch = true;
+    if (kTrack) mark_changed(w.tb, w.tk, w.cur, v);
+  }
+}
+
+template <bool kTrack, bool kBits>
+__device__ __forceinline__ void tell_ub_v(const Sweep& w, int v, int cand, int lb_seen,
+                                          int ub_seen, Flags& f) {
+  if (!kBits || v < w.tb.bit0) {
+    tell_ub<kTrack>(w, v, cand, lb_seen, ub_seen, f);
+    return;
+  }
+  if (cand >= ub_seen) return;
+  if (cand < lb_seen) {
+    f.fl = true;
+    return;
+  }
+  const int q = v - w.tb.bit0;
+  const uint32_t m = 1u << (q & 31);
+  if (atom_and_old(&w.st[w.tb.bit0 + (q >> 5)].y, ~m) & m) {
+    f.ch = true;
+    if (kTrack) mark_changed(w.tb, w.tk, w.cur, v);
+  }
+}
+
 // Temporal row x + d <= y: ub(x) <= ub(y) - d and lb(y) >= lb(x) + d
 // (the [[x + y <= c]] compilation of Sec. 2 with y negated).  The common case
 // (nothing to tell) costs one branch.
@@ -437,8 +536,9 @@ __device__ __forceinline__ bool rule_quiet(int2 B, int g1, int g2, int d) {
 // settles) sit behind one branch.  kQuiet: rows that cannot tell anything
 // (rule_quiet) leave before the rule; that pays where loads are slow (tables
 // read from global memory) and costs where issue is the limit (tables in
-// shared memory), so the kernels for global tables use it.
-template <bool kTrack, bool kQuiet>
+// shared memory), so the kernels for global tables use it.  kBits: the
+// model may keep b as a bit (global tables only; else a plain interval load).
+template <bool kTrack, bool kQuiet, bool kBits = kQuiet>
 __device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f) {
   const int x = row.x & 0xffff, y = row.x >> 16;
   const int b = row.y & 0xffff, d = static_cast<int>(row.y) >> 16;
@@ -449,7 +549,7 @@ __device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f
   }
   f.evals += 1;
   f.bytes += 40;
-  const int2 X = ld_dom(w.st, x), Y = ld_dom(w.st, y), B = ld_dom(w.st, b);
+  const int2 X = ld_dom(w.st, x), Y = ld_dom(w.st, y), B = ld_var<kBits>(w.st, w.tb.bit0, b);
   if (kQuiet && X.x <= X.y && Y.x <= Y.y && rule_quiet(B, Y.x - X.y, X.x - Y.y, d)) return;
   int nlx = X.x, nux = X.y, nly = Y.x, nuy = Y.y, nlb = B.x, nub = B.y;
   reified_rule(X, Y, B, d, nlx, nux, nly, nuy, nlb, nub);
@@ -458,8 +558,8 @@ __device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f
     tell_ub<kTrack>(w, x, nux, X.x, X.y, f);
     tell_lb<kTrack>(w, y, nly, Y.x, Y.y, f);
     tell_ub<kTrack>(w, y, nuy, Y.x, Y.y, f);
-    tell_lb<kTrack>(w, b, nlb, B.x, B.y, f);
-    tell_ub<kTrack>(w, b, nub, B.x, B.y, f);
+    tell_lb_v<kTrack, kBits>(w, b, nlb, B.x, B.y, f);
+    tell_ub_v<kTrack, kBits>(w, b, nub, B.x, B.y, f);
   }
 }
 
@@ -467,7 +567,7 @@ __device__ __forceinline__ void eval_reified(const Sweep& w, uint2 row, Flags& f
 // b1 <=> (x <= y and y < x + d1) and b2 <=> (y <= x and x < y + d2) (the
 // overlap Booleans b_{i,j} and b_{j,i} of the scheduling model): both rules on
 // one snapshot, so x and y are loaded once for two rows.
-template <bool kTrack, bool kQuiet>
+template <bool kTrack, bool kQuiet, bool kBits = kQuiet>
 __device__ __forceinline__ void eval_reified_pair(const Sweep& w, uint4 row, Flags& f) {
   const int x = row.x & 0xffff, y = row.x >> 16;
   const int b1 = row.y & 0xffff, d1 = static_cast<int>(row.y) >> 16;
@@ -481,7 +581,7 @@ __device__ __forceinline__ void eval_reified_pair(const Sweep& w, uint4 row, Fla
   f.evals += 2;
   f.bytes += 80;
   const int2 X = ld_dom(w.st, x), Y = ld_dom(w.st, y);
-  const int2 B1 = ld_dom(w.st, b1), B2 = ld_dom(w.st, b2);
+  const int2 B1 = ld_var<kBits>(w.st, w.tb.bit0, b1), B2 = ld_var<kBits>(w.st, w.tb.bit0, b2);
   if (kQuiet) {  // neither rule can tell anything (rule 2 swaps x and y)
     const int g1 = Y.x - X.y, g2 = X.x - Y.y;
     if (X.x <= X.y && Y.x <= Y.y && rule_quiet(B1, g1, g2, d1) && rule_quiet(B2, g2, g1, d2))
@@ -497,10 +597,10 @@ __device__ __forceinline__ void eval_reified_pair(const Sweep& w, uint4 row, Fla
     tell_ub<kTrack>(w, x, nux, X.x, X.y, f);
     tell_lb<kTrack>(w, y, nly, Y.x, Y.y, f);
     tell_ub<kTrack>(w, y, nuy, Y.x, Y.y, f);
-    tell_lb<kTrack>(w, b1, nlb1, B1.x, B1.y, f);
-    tell_ub<kTrack>(w, b1, nub1, B1.x, B1.y, f);
-    tell_lb<kTrack>(w, b2, nlb2, B2.x, B2.y, f);
-    tell_ub<kTrack>(w, b2, nub2, B2.x, B2.y, f);
+    tell_lb_v<kTrack, kBits>(w, b1, nlb1, B1.x, B1.y, f);
+    tell_ub_v<kTrack, kBits>(w, b1, nub1, B1.x, B1.y, f);
+    tell_lb_v<kTrack, kBits>(w, b2, nlb2, B2.x, B2.y, f);
+    tell_ub_v<kTrack, kBits>(w, b2, nub2, B2.x, B2.y, f);
   }
 }
 
@@ -520,7 +620,7 @@ __device__ __forceinline__ bool skip_linear_long(const Sweep& w, int r, int lane
 }
 
 // Long row r with header h; its term k at tp[k] (shared or global memory).
-template <bool kTrack>
+template <bool kTrack, bool kBits>
 __device__ __forceinline__ void eval_linear_warp_at(const Sweep& w, int4 h,
                                                     const uint32_t* __restrict__ tp, int lane,
                                                     Flags& f) {
@@ -537,7 +637,7 @@ __device__ __forceinline__ void eval_linear_warp_at(const Sweep& w, int4 h,
   for (int k = lane; k < len; k += 32) {
     const uint32_t t = tp[k];
     const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
-    const int2 D = ld_dom(st, v);
+    const int2 D = ld_var<kBits>(st, w.tb.bit0, v);
     const int mt = (pos || a > 0) ? a * D.x : a * D.y;
     const int sp = (pos || a > 0) ? a * (D.y - D.x) : a * (D.x - D.y);
     S += mt;
@@ -568,9 +668,9 @@ __device__ __forceinline__ void eval_linear_warp_at(const Sweep& w, int4 h,
         const uint32_t t = tp[k];
         if ((static_cast<int>(t) >> 16) <= slack0) continue;
         v = t & 0xffff;
-        D = ld_dom(st, v);
+        D = ld_var<kBits>(st, w.tb.bit0, v);
       }
-      if (D.x == 0 && D.y == 1) tell_ub<kTrack>(w, v, 0, D.x, D.y, f);
+      if (D.x == 0 && D.y == 1) tell_ub_v<kTrack, kBits>(w, v, 0, D.x, D.y, f);
     }
     return;
   }
@@ -585,7 +685,7 @@ __device__ __forceinline__ void eval_linear_warp_at(const Sweep& w, int4 h,
       const uint32_t t = tp[k];
       v = t & 0xffff;
       a = static_cast<int>(t) >> 16;
-      D = ld_dom(st, v);
+      D = ld_var<kBits>(st, w.tb.bit0, v);
     }
     const int mt = a > 0 ? a * D.x : a * D.y;
     const int slack = c - (S - mt);
@@ -611,7 +711,7 @@ __device__ __forceinline__ bool skip_linear_short(const Sweep& w, int r, Flags& 
 }
 
 // Short row with header h; its term k at tp[32 k] (shared or global memory).
-template <bool kTrack>
+template <bool kTrack, bool kBits>
 __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
                                                       const uint32_t* __restrict__ tp, Flags& f) {
   int2* st = w.st;
@@ -624,7 +724,7 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
     for (int k = 0; k < len; ++k) {
       const uint32_t t = tp[32 * k];
       const int a = static_cast<int>(t) >> 16;
-      const int2 D = ld_dom(st, t & 0xffff);
+      const int2 D = ld_var<kBits>(st, w.tb.bit0, t & 0xffff);
       S += a * D.x;
       span = max(span, a * (D.y - D.x));
     }
@@ -633,7 +733,7 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
     for (int k = 0; k < len; ++k) {
       const uint32_t t = tp[32 * k];
       const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
-      const int2 D = ld_dom(st, v);
+      const int2 D = ld_var<kBits>(st, w.tb.bit0, v);
       S += a > 0 ? a * D.x : a * D.y;
       span = max(span, a > 0 ? a * (D.y - D.x) : a * (D.x - D.y));
     }
@@ -653,15 +753,15 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
       const uint32_t t = tp[32 * k];
       if ((static_cast<int>(t) >> 16) <= slack0) continue;
       const int v = t & 0xffff;
-      const int2 D = ld_dom(st, v);
-      if (D.x == 0 && D.y == 1) tell_ub<kTrack>(w, v, 0, D.x, D.y, f);
+      const int2 D = ld_var<kBits>(st, w.tb.bit0, v);
+      if (D.x == 0 && D.y == 1) tell_ub_v<kTrack, kBits>(w, v, 0, D.x, D.y, f);
     }
     return;
   }
   for (int k = 0; k < len; ++k) {
     const uint32_t t = tp[32 * k];
     const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
-    const int2 D = ld_dom(st, v);
+    const int2 D = ld_var<kBits>(st, w.tb.bit0, v);
     const int mt = a > 0 ? a * D.x : a * D.y;
     const int slack = c - (S - mt);
     if (a > 0) {
@@ -680,15 +780,16 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
 // the table in shared memory reified, temporal, linear; in global memory
 // linear, reified, temporal -- each the faster of the six orders measured
 // there (the second saves iterations on 120-task models, the first is
-// faster for the depth-first searches of 30-task models).
-template <bool kTrack, bool kQuiet>
+// faster for the depth-first searches of 30-task models).  kBits: the model
+// keeps Booleans as bits (global tables only).
+template <bool kTrack, bool kQuiet, bool kBits>
 __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags& f) {
   const Tab& tb = w.tb;
   if (kQuiet) {  // tables in global memory: linear, reified, temporal
     for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) {
       if (skip_linear_short<kTrack>(w, r, f)) continue;
       const int4 h = tb.lin[r];
-      eval_linear_thread_at<kTrack>(w, h, tb.terms + h.y, f);
+      eval_linear_thread_at<kTrack, kBits>(w, h, tb.terms + h.y, f);
     }
     // long rows, then blocks of 32 reified pairs, claimed by whole warps from
     // the sweep's counter: rows of uneven cost (lengths, skipped rows, L2
@@ -701,30 +802,32 @@ __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags
       if (q < tb.n_lin_long) {
         if (skip_linear_long<kTrack>(w, q, tm.lane, f)) continue;
         const int4 h = tb.lin_long[q];
-        eval_linear_warp_at<kTrack>(w, h, tb.terms_long + h.y, tm.lane, f);
+        eval_linear_warp_at<kTrack, kBits>(w, h, tb.terms_long + h.y, tm.lane, f);
       } else if (q < tb.n_lin_long + n_blocks) {
         const int r = ((q - tb.n_lin_long) << 5) + tm.lane;
-        if (r < tb.n_rfp) eval_reified_pair<kTrack, kQuiet>(w, tb.rfp[r], f);
+        if (r < tb.n_rfp) eval_reified_pair<kTrack, kQuiet, kBits>(w, tb.rfp[r], f);
       } else {
         break;
       }
     }
-    for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack, kQuiet>(w, tb.rf[r], f);
+    for (int r = tm.tid; r < tb.n_rf; r += tm.nthr)
+      eval_reified<kTrack, kQuiet, kBits>(w, tb.rf[r], f);
     for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
   } else {  // tables in shared memory: reified, temporal, linear
     for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr)
-      eval_reified_pair<kTrack, kQuiet>(w, tb.rfp[r], f);
-    for (int r = tm.tid; r < tb.n_rf; r += tm.nthr) eval_reified<kTrack, kQuiet>(w, tb.rf[r], f);
+      eval_reified_pair<kTrack, kQuiet, kBits>(w, tb.rfp[r], f);
+    for (int r = tm.tid; r < tb.n_rf; r += tm.nthr)
+      eval_reified<kTrack, kQuiet, kBits>(w, tb.rf[r], f);
     for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
     for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) {
       if (skip_linear_short<kTrack>(w, r, f)) continue;
       const int4 h = tb.lin[r];
-      eval_linear_thread_at<kTrack>(w, h, tb.terms + h.y, f);
+      eval_linear_thread_at<kTrack, kBits>(w, h, tb.terms + h.y, f);
     }
     for (int r = tm.warp; r < tb.n_lin_long; r += tm.nwarps) {
       if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
       const int4 h = tb.lin_long[r];
-      eval_linear_warp_at<kTrack>(w, h, tb.terms_long + h.y, tm.lane, f);
+      eval_linear_warp_at<kTrack, kBits>(w, h, tb.terms_long + h.y, tm.lane, f);
     }
   }
 }
@@ -885,7 +988,7 @@ __device__ __forceinline__ void sweep_rows_streamed(const Sweep& w, const Team& 
             const int r = s.first + i;
             if (skip_linear_short<kTrack>(w, r, f)) continue;
             const int4 h = tb.lin[r];
-            eval_linear_thread_at<kTrack>(w, h, T + (h.y - s.term_base), f);
+            eval_linear_thread_at<kTrack, true>(w, h, T + (h.y - s.term_base), f);
           }
           break;
         }
@@ -897,7 +1000,7 @@ __device__ __forceinline__ void sweep_rows_streamed(const Sweep& w, const Team& 
             const int r = s.first + i;
             if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
             const int4 h = tb.lin_long[r];
-            eval_linear_warp_at<kTrack>(w, h, T + (h.y - base), tm.lane, f);
+            eval_linear_warp_at<kTrack, true>(w, h, T + (h.y - base), tm.lane, f);
           }
           break;
         }
@@ -958,7 +1061,11 @@ __device__ __forceinline__ void count_sweeps(const Tab& tb, const Team& tm, FixC
 // kGlobal: the table is in global memory; kStream (with kGlobal): its rows
 // come in segments through the team's stream *sm, else they are read where
 // tb points.  A stream that lost a copy ends the loop with kError.
-template <bool kTrack, bool kGlobal = false, bool kStream = false>
+// kBitSel (global tables): kBitsAny reads the model's layout at run time,
+// kBitsNo / kBitsYes compile one sweep (models known to keep no Booleans as
+// bits / to keep some).
+constexpr int kBitsNo = 0, kBitsYes = 1, kBitsAny = 2;
+template <bool kTrack, bool kGlobal = false, bool kStream = false, int kBitSel = kBitsAny>
 __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team& tm, FixCtrl* fc,
                                              const Track& tk, bool full, int max_iter,
                                              int& iters, Streamer* sm = nullptr) {
@@ -985,8 +1092,10 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
     Flags f{false, false, 0, 0};
     if (kStream)
       sweep_rows_streamed<kTrack>(w, tm, f, *sm);
+    else if (kGlobal && kBitSel != kBitsNo && (kBitSel == kBitsYes || tb.bit0 < tb.n_vars))
+      sweep_rows<kTrack, kGlobal, kGlobal>(w, tm, f);  // Booleans kept as bits
     else
-      sweep_rows<kTrack, kGlobal>(w, tm, f);
+      sweep_rows<kTrack, kGlobal, false>(w, tm, f);
     if (kTrack) {  // rows skipped vary: count what ran
       const int ev = __reduce_add_sync(0xffffffffu, f.evals);
       const int by = __reduce_add_sync(0xffffffffu, f.bytes);
@@ -1018,10 +1127,7 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
   }
   count_sweeps<kTrack>(tb, tm, fc, it);
   bool empty = false;
-  for (int v = tm.tid; v < tb.n_vars; v += tm.nthr) {
-    const int2 D = ld_dom(st, v);
-    empty |= D.x > D.y;
-  }
+  for (int sl = tm.tid; sl < tb.n_slots; sl += tm.nthr) empty |= slot_empty(ld_dom(st, sl), sl, tb.bit0);
   iters = it;
   return team_bar_or(tm.bar, tm.nthr, empty) ? kFailed : kFixpoint;
 }

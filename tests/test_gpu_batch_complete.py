@@ -92,14 +92,28 @@ def test_slot_shapes_and_table_placements_agree_with_the_oracle():
 
 
 def test_many_small_slots_and_a_large_model_alone():
-    """Up to 15 one-warp teams per CTA on 8-task models; a 120-task model
-    (its store alone fills half the shared memory) with one team per CTA, and
-    refused with several."""
+    """Up to 15 one-warp teams per CTA on 8-task models; a 120-task model:
+    with interval stores (116 KB, half the shared memory) with one team per
+    CTA, and refused with several; with its Booleans as bits (a 4.6 KB store)
+    in four teams per CTA."""
     _same_as_oracle([config_instance("tiny8", s) for s in range(40)], 300, [
         dict(teams_per_cta=8, threads=64), dict(teams_per_cta=12, threads=32),
         dict(teams_per_cta=15, threads=32)])
-    big = _same_as_oracle([config_instance("j120", 0), config_instance("tiny8", 3)], 10, [
+    _same_as_oracle([config_instance("j120", 0), config_instance("tiny8", 3)], 10, [
         dict(), dict(teams_per_cta=1, threads=512)])
+    bits = [pccp.Model.from_rcpsp(config_instance("j120", 0), bool_store=1),
+            pccp.Model.from_rcpsp(config_instance("tiny8", 3))]
+    rb = pccp.solve_batch(bits, strategy=pccp.PCCP_FIRST_FAIL, node_limit=10, teams_per_cta=4,
+                          threads=256)
+    ob = oracle.solve(rcpsp_model(config_instance("j120", 0)), strategy=oracle.FIRST_FAIL,
+                      node_limit=10)
+    assert (rb[0]["nodes"], rb[0]["fails"]) == (ob["nodes"], ob["fails"])
+    big = [pccp.Model.from_rcpsp(config_instance("j120", 0), bool_store=-1),
+           pccp.Model.from_rcpsp(config_instance("tiny8", 3))]
+    r = pccp.solve_batch(big, strategy=pccp.PCCP_FIRST_FAIL, node_limit=10, teams_per_cta=1)
+    o = oracle.solve(rcpsp_model(config_instance("j120", 0)), strategy=oracle.FIRST_FAIL,
+                     node_limit=10)
+    assert (r[0]["nodes"], r[0]["fails"]) == (o["nodes"], o["fails"])
     with pytest.raises(pccp.PccpError) as e:
         pccp.solve_batch(big, node_limit=5, teams_per_cta=4)
     assert e.value.code == pccp.PCCP_ERR_SMEM

@@ -211,11 +211,22 @@ def test_edge_cases():
 def test_store_size_limits():
     """A store larger than shared memory is refused on the host; a store near
     the limit (table read from global memory) is still bit-exact."""
-    big = pccp.Model([0] * 40000, [1] * 40000)
+    big = pccp.Model([0] * 40000, [1] * 40000, bool_store=-1)
     assert big.info.max_store_vars < 40000
     with pytest.raises(pccp.PccpError) as e:
         run(big, np.zeros((1, 40000)), np.ones((1, 40000)))
     assert e.value.code == pccp.PCCP_ERR_SMEM
+    # the same 40,000 Booleans kept as bits (the default: intervals would not fit)
+    bits = pccp.Model([0] * 40000, [1] * 40000)
+    assert bits.info.bool_vars == 40000 and bits.info.store_bytes == 8 * 1250
+    lb = np.zeros((2, 40000), dtype=np.int32)
+    ub = np.ones((2, 40000), dtype=np.int32)
+    lb[0, ::3] = 1
+    ub[0, 1::3] = 0
+    lb[1, 7], ub[1, 7] = 1, 0
+    st, glb, gub, _ = run(bits, lb, ub)
+    assert st.tolist() == [0, 1]
+    assert np.array_equal(glb[0], lb[0]) and np.array_equal(gub[0], ub[0])
     n = int(0.9 * pccp.Model([0], [1]).info.max_store_vars)
     g = np.random.default_rng(4)
     lb0 = [0] * n
