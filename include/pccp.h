@@ -135,6 +135,9 @@ typedef struct {
   int32_t bool_vars;        /* Booleans kept as bits (see pccp_model_desc.bool_store) */
   int32_t store_bytes;      /* shared memory of one store: 8 B per other variable and
                                8 B per 32 Booleans kept as bits */
+  int32_t temporal_levels;  /* topological levels of the temporal rows (the longest
+                               chain of rows), 0 when they have a cycle (see
+                               pccp_launch_config.temporal_levels) */
 } pccp_model_info;
 
 int pccp_model_get_info(const pccp_model* model, pccp_model_info* info);
@@ -176,6 +179,15 @@ typedef struct {
                              (through L1/L2); 1 stream them through a ring of
                              shared-memory buffers by TMA bulk copies, segment by
                              segment, every sweep.  Same fixed point either way. */
+  int32_t temporal_levels; /* models whose temporal rows x + d <= y form an acyclic
+                              graph: 1 two warps of a team carry the bounds along
+                              its chains in one pass each sweep (rows grouped by
+                              topological level of x: lower bounds in increasing
+                              levels, upper bounds in decreasing ones); -1 a thread
+                              per row, which moves a bound one row per sweep; 0 the
+                              library's choice (levels in propagation; in searches
+                              only for tables read from global memory).  Same fixed
+                              point either way (Sec. 3). */
 } pccp_launch_config;
 
 /* pccp_propagate with an explicit launch shape (cfg may be NULL) and an
@@ -275,6 +287,10 @@ typedef struct {
                                subproblem a team hands its shallowest open right branch
                                to the queue at each branching while teams wait for
                                work (0 = the library's choice, 4; < 0 = never) */
+  int32_t temporal_levels;  /* as in pccp_launch_config (0: the library's choice: levels
+                               for tables read from global memory only, since the
+                               nodes of a search are mostly one decision away from a
+                               fixed point, where the levels save few sweeps) */
 } pccp_solve_opts;
 
 /* Counters and outcome of one search.  A node is every store propagated,

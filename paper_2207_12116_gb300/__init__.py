@@ -236,11 +236,14 @@ def _skip(skip_stable):
 
 
 def launch_config(team_threads=0, teams_per_cta=0, ctas_per_sm=0, max_iterations=0,
-                  skip_stable=None, stream_table=False):
+                  skip_stable=None, stream_table=False, temporal_levels=None):
     """stream_table=True streams a table too large for shared memory through
-    shared-memory buffers (TMA bulk copies) instead of reading it in place."""
+    shared-memory buffers (TMA bulk copies) instead of reading it in place.
+    temporal_levels: None the library's choice, True walk the temporal rows
+    level by level, False a thread per row."""
     return _abi.pccp_launch_config(team_threads, teams_per_cta, ctas_per_sm, max_iterations,
-                                   _skip(skip_stable), int(bool(stream_table)))
+                                   _skip(skip_stable), int(bool(stream_table)),
+                                   _skip(temporal_levels))
 
 
 def propagate(model: Model, lb, ub, status=None, iterations=None, config=None, stream=None,
@@ -308,12 +311,13 @@ def propagate_host(model: Model, lb, ub, status=None, iterations=None, chunk_sto
 
 def _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
           skip_stable=None, policy=None, stream_table=False, teams_per_cta=0,
-          props_per_thread=0, queue_granularity=0, donate_nodes=0):
+          props_per_thread=0, queue_granularity=0, donate_nodes=0, temporal_levels=None):
     return _abi.pccp_solve_opts(strategy, mode, int(bool(deterministic)), obj_ub, node_limit,
                                 time_limit_ms, threads, blocks, _skip(skip_stable),
                                 int(bool(stream_table)),
                                 policy.handle if policy is not None else None,
-                                teams_per_cta, props_per_thread, queue_granularity, donate_nodes)
+                                teams_per_cta, props_per_thread, queue_granularity, donate_nodes,
+                                _skip(temporal_levels))
 
 
 def _result_dict(r, w):
@@ -329,10 +333,10 @@ def _result_dict(r, w):
 def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, deterministic=True,
           obj_ub=INT32_MAX, node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None,
           skip_stable=None, policy=None, stream_table=False, props_per_thread=0,
-          queue_granularity=0, donate_nodes=0):
+          queue_granularity=0, donate_nodes=0, temporal_levels=None):
     o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
               skip_stable, policy, stream_table, 0, props_per_thread, queue_granularity,
-              donate_nodes)
+              donate_nodes, temporal_levels)
     w = np.zeros(model.n_vars, dtype=np.int32)
     r = _abi.pccp_result()
     r.witness = w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
@@ -344,14 +348,15 @@ def solve(model: Model, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, determini
 def solve_batch(models, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
                 node_limit=0, time_limit_ms=0, threads=0, blocks=0, stream=None, noalloc=False,
                 skip_stable=None, policy=None, stream_table=False, teams_per_cta=0,
-                props_per_thread=0, deterministic=True, queue_granularity=0, donate_nodes=0):
+                props_per_thread=0, deterministic=True, queue_granularity=0, donate_nodes=0,
+                temporal_levels=None):
     """Solve many models in one launch.  deterministic=True: one team per
     model in the sequential order; False: every team over one shared queue of
     subproblems of all models, with work donation.  noalloc=True uses the
     allocation-free entry point (fixed device scratch; see include/pccp.h)."""
     o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, threads, blocks,
               skip_stable, policy, stream_table, teams_per_cta, props_per_thread,
-              queue_granularity, donate_nodes)
+              queue_granularity, donate_nodes, temporal_levels)
     n = len(models)
     ws = [np.zeros(m.n_vars, dtype=np.int32) for m in models]
     res = (_abi.pccp_result * n)()
@@ -383,9 +388,11 @@ class Batch:
 
     def solve_async(self, strategy=PCCP_INPUT_ORDER, mode=PCCP_OPTIMISE, obj_ub=INT32_MAX,
                     node_limit=0, time_limit_ms=0, stream=None, skip_stable=None, policy=None,
-                    deterministic=True, queue_granularity=0, donate_nodes=0):
+                    deterministic=True, queue_granularity=0, donate_nodes=0,
+                    temporal_levels=None):
         o = _opts(strategy, mode, deterministic, obj_ub, node_limit, time_limit_ms, 0, 0,
-                  skip_stable, policy, False, 0, 0, queue_granularity, donate_nodes)
+                  skip_stable, policy, False, 0, 0, queue_granularity, donate_nodes,
+                  temporal_levels)
         check(pccp_batch_solve_async(self.handle, o, _stream_ptr(stream)), "pccp_batch_solve_async")
 
     def results(self, stream=None):

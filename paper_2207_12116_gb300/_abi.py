@@ -49,12 +49,13 @@ class pccp_model_info(ctypes.Structure):
     _fields_ = [("n_vars", I32), ("n_temporal", I32), ("n_linear", I32), ("n_terms", I32),
                 ("n_reified", I32), ("table_bytes", I32), ("bytes_per_sweep", I64),
                 ("max_store_vars", I32), ("n_segments", I32), ("reordered", I32),
-                ("bool_vars", I32), ("store_bytes", I32)]
+                ("bool_vars", I32), ("store_bytes", I32), ("temporal_levels", I32)]
 
 
 class pccp_launch_config(ctypes.Structure):
     _fields_ = [("team_threads", I32), ("teams_per_cta", I32), ("ctas_per_sm", I32),
-                ("max_iterations", I32), ("skip_stable", I32), ("stream_table", I32)]
+                ("max_iterations", I32), ("skip_stable", I32), ("stream_table", I32),
+                ("temporal_levels", I32)]
 
 
 class pccp_solve_opts(ctypes.Structure):
@@ -62,7 +63,7 @@ class pccp_solve_opts(ctypes.Structure):
                 ("node_limit", I64), ("time_limit_ms", I64), ("threads", I32), ("blocks", I32),
                 ("skip_stable", I32), ("stream_table", I32), ("policy", P),
                 ("teams_per_cta", I32), ("props_per_thread", I32), ("queue_granularity", I32),
-                ("donate_nodes", I32)]
+                ("donate_nodes", I32), ("temporal_levels", I32)]
 
 
 class pccp_policy_weights(ctypes.Structure):

@@ -32,6 +32,9 @@ struct PropArgs {
   int table_global;   // 1: rows are read from the device image (too big for shared memory)
   int stream_stages;  // table_global: buffers of each team's stream (0: rows read in place)
   int reordered;      // 1: st uses the library's variable order (internal_of after the root)
+  uint32_t tlev_bytes;  // table_global, in place: temporal levels staged per CTA (0: none)
+  uint32_t off_tlev;    // their offset in the image
+  int levels;           // temporal levels: bit 0 staged tables, bit 1 global ones
 };
 
 // Per-team scalars of k_propagate (shared memory).
@@ -48,10 +51,12 @@ struct PropCtrl {
 template <int kMaxThreads, int kMinBlocks, bool kTrack, bool kGlobal, bool kStream>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  // shared memory: [table image | kGlobal: one stream region per team, or none]
+  // shared memory: [table image | kGlobal: one stream region per team, or
+  //                 the temporal levels, or none]
   //                [mbarrier 16 B][PropCtrl x teams][change words x teams][stores]
   const size_t stream_region = stream_bytes(a.stream_stages);
-  const size_t img_bytes = kGlobal ? stream_region * a.teams : a.image_bytes;
+  const uint32_t tl_bytes = kGlobal && !kStream ? a.tlev_bytes : 0u;
+  const size_t img_bytes = kGlobal ? stream_region * a.teams + tl_bytes : a.image_bytes;
   uint8_t* img = smem;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + img_bytes);
   PropCtrl* ctrl_base = reinterpret_cast<PropCtrl*>(smem + img_bytes + 16);
@@ -64,6 +69,12 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   if (!kGlobal) {
     if (threadIdx.x == 0) mbar_init(mbar, 1);
     ok = load_image(img, a.image, a.image_bytes, mbar, 0);
+  } else if (tl_bytes != 0u) {  // 16-byte multiples at 16-byte aligned offsets
+    const int4* src = reinterpret_cast<const int4*>(a.image + a.off_tlev);
+    int4* dst = reinterpret_cast<int4*>(smem);
+    const uint32_t n16 = a.tlev_bytes / 16u;
+    for (uint32_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
   }
 
   const int team_id = threadIdx.x / a.team_size;
@@ -76,7 +87,13 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_propagate(PropArgs 
   tm.nwarps = a.team_size >> 5;
   PropCtrl* ctrl = ctrl_base + team_id;
   int2* st = st_base + static_cast<size_t>(team_id) * a.n_slots;
-  const Tab tb = make_tab(kGlobal ? a.image : img);
+  Tab tb = make_tab(kGlobal ? a.image : img, a.levels & (kGlobal ? 2 : 1));
+  if (kGlobal) {  // the levels from shared memory, or the rows one thread each
+    if (tl_bytes != 0u)
+      tab_levels_at(tb, smem);
+    else
+      tb.n_tlev = 0;
+  }
   const Track tk = make_track(track_base + static_cast<size_t>(tw16) * team_id, tb.n_vars,
                               tb.n_lin + tb.n_lin_long);
   const int nv = a.n_vars;

@@ -61,6 +61,7 @@ struct EpsArgs {
   const PolicyDev* policy;
   int64_t node_limit;
   int64_t time_limit_ns;
+  int levels;  // temporal levels: bit 0 staged tables, bit 1 global ones
 };
 
 struct EpsCtrl {
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(1024) k_eps_expand(EpsArgs a) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && a.g->t0 == 0)
     atomicCAS(&a.g->t0, 0ull, static_cast<unsigned long long>(eps_now_ns()));
   const Team tm = eps_team(a, team_id);
-  const Tab tb = make_tab(kGlobal ? a.image : sm.img);
+  const Tab tb = make_tab(kGlobal ? a.image : sm.img, a.levels & (kGlobal ? 2 : 1));
   const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
   Streamer stream;
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(1024) k_eps_solve(EpsArgs a) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && a.g->t0 == 0)
     atomicCAS(&a.g->t0, 0ull, static_cast<unsigned long long>(eps_now_ns()));
   const Team tm = eps_team(a, team_id);
-  const Tab tb = make_tab(kGlobal ? a.image : sm.img);
+  const Tab tb = make_tab(kGlobal ? a.image : sm.img, a.levels & (kGlobal ? 2 : 1));
   const Track tk = make_track(sm.track, tb.n_vars, tb.n_lin + tb.n_lin_long);
   const int team_gid = blockIdx.x * a.teams + team_id;
   Streamer stream;

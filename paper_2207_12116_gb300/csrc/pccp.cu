@@ -99,6 +99,7 @@ struct SolveArgs {
   int teams;
   uint32_t slot_bytes;
   uint32_t off_track, off_x, off_stack, off_store;  // byte offsets inside a slot
+  int levels;  // temporal levels: bit 0 with tables in shared memory, bit 1 in global memory
 };
 
 // Broadcast slots of one team's search.  Each slot has one writer (thread 0)
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs a) {
     } else {
       __syncthreads();
     }
-    const Tab tb = make_tab(kGlobal ? d.image : img);
+    const Tab tb = make_tab(kGlobal ? d.image : img, a.levels & (kGlobal ? 2 : 1));
     const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
     if (kStream) {  // the previous model's prefetched copies land first
       if (open) seq = stream_close(stream);
@@ -460,12 +461,12 @@ __global__ void __launch_bounds__(1024) k_solve_slots(SolveArgs a) {
         return;  // this team stops; its mbarrier phase may still be pending
       }
       parity ^= 1u;
-      const Tab tb = make_tab(img);
+      const Tab tb = make_tab(img, a.levels & 1);
       const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
       team_dfs<kTrackS, kLearned, false, false>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
                                                 a.witness + d.witness_off, out, X, nullptr);
     } else {
-      const Tab tb = make_tab(d.image);
+      const Tab tb = make_tab(d.image, a.levels & 2);
       const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
       team_dfs<kTrackG, kLearned, true, false>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
                                                a.witness + d.witness_off, out, X, nullptr);
@@ -484,9 +485,18 @@ struct Packed {
   int64_t bytes_per_sweep;
   uint32_t core_bytes, track_bytes;  // image prefixes copied to shared memory
   int32_t bit0, n_slots;             // store layout
+  int32_t n_tlev;                    // levels of the temporal rows (0: not acyclic)
+  uint32_t tlev_bytes;               // their section (the end of the core prefix)
 };
 
 size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
+
+// Where the temporal levels run (bit 0: tables in shared memory, bit 1:
+// tables in global memory) for an option value (1 on, -1 off, 0 the
+// library's choice: everywhere in propagation, global tables in searches).
+int levels_mask(int32_t opt, bool propagation) {
+  return opt > 0 ? 3 : opt < 0 ? 0 : (propagation ? 3 : 2);
+}
 
 }  // namespace
 
@@ -510,6 +520,8 @@ struct pccp_model {
   int32_t max_iter;  // every changing iteration narrows some bound by >= 1
   int32_t max_decisions;  // bound on a search path's length (decision stack entries)
   int32_t bit0, n_slots;  // store layout: Booleans from bit0 on as bits; int2 slots per store
+  int32_t n_tlev;         // levels of the temporal rows (0: not acyclic)
+  uint32_t tlev_bytes;    // their section, the last tlev_bytes of the core prefix
   uint8_t* d_mem;    // image, then root int2[n_vars]
   int2* d_root;
   HostPipe* pipe = nullptr;  // pccp_propagate_host's streams and slots (lazy)
@@ -983,6 +995,48 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p, int32_t bit0 = -1) {
     }
   }
 
+  // temporal rows in topological levels, when they form an acyclic graph:
+  // the level of variable v is the length of the longest chain of rows
+  // ending at v; rows are grouped by the level of their x.  Within a level no
+  // row's y is another row's x, so a level's rows may run together: levels in
+  // increasing order carry every lower bound along the chains in one pass,
+  // in decreasing order every upper bound.
+  std::vector<int32_t> TLEV_OFF;
+  std::vector<uint2> TLEV;
+  if (!T.empty()) {
+    std::vector<int32_t> indeg(nv, 0), level(nv, 0), order;
+    std::vector<std::vector<int32_t>> out(nv);
+    bool acyclic = true;
+    for (size_t r = 0; r < T.size(); ++r) {
+      const int32_t x = static_cast<int32_t>(T[r].x & 0xffffu), y = static_cast<int32_t>(T[r].x >> 16);
+      if (x == y) acyclic = false;
+      out[x].push_back(static_cast<int32_t>(r));
+      ++indeg[y];
+    }
+    for (int64_t v = 0; v < nv && acyclic; ++v)
+      if (indeg[v] == 0 && !out[v].empty()) order.push_back(static_cast<int32_t>(v));
+    size_t done_rows = 0;
+    for (size_t q = 0; q < order.size() && acyclic; ++q) {
+      const int32_t v = order[q];
+      for (int32_t r : out[v]) {
+        const int32_t y = static_cast<int32_t>(T[r].x >> 16);
+        level[y] = std::max(level[y], level[v] + 1);
+        ++done_rows;
+        if (--indeg[y] == 0 && !out[y].empty()) order.push_back(y);
+      }
+    }
+    if (acyclic && done_rows == T.size()) {
+      int32_t n_lev = 0;
+      for (const uint2& row : T) n_lev = std::max(n_lev, level[row.x & 0xffffu] + 1);
+      TLEV_OFF.assign(n_lev + 1, 0);
+      for (const uint2& row : T) ++TLEV_OFF[level[row.x & 0xffffu] + 1];
+      for (int32_t l = 0; l < n_lev; ++l) TLEV_OFF[l + 1] += TLEV_OFF[l];
+      std::vector<int32_t> fill(TLEV_OFF.begin(), TLEV_OFF.end() - 1);
+      TLEV.resize(T.size());
+      for (const uint2& row : T) TLEV[fill[level[row.x & 0xffffu]]++] = row;
+    }
+  }
+
   TableHeader h;
   std::memset(&h, 0, sizeof(h));
   h.n_vars = static_cast<int32_t>(nv);
@@ -1019,6 +1073,10 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p, int32_t bit0 = -1) {
   off = align16(off + static_cast<size_t>(d->n_branch) * sizeof(int32_t));
   h.off_bstat = static_cast<int32_t>(off);
   off = align16(off + BST.size() * sizeof(BranchStatic));
+  h.off_tlev = static_cast<int32_t>(off);
+  h.n_tlev = TLEV_OFF.empty() ? 0 : static_cast<int32_t>(TLEV_OFF.size()) - 1;
+  off = align16(off + TLEV_OFF.size() * sizeof(int32_t));
+  off = align16(off + TLEV.size() * sizeof(uint2));
   h.core_bytes = static_cast<int32_t>(off);  // what the eventless kernels copy
   h.off_adj_off = static_cast<int32_t>(off);
   off = align16(off + ADJ_OFF.size() * sizeof(int32_t));
@@ -1103,6 +1161,11 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p, int32_t bit0 = -1) {
     std::memcpy(p->image.data() + h.off_bstat, BST.data(), BST.size() * sizeof(BranchStatic));
   if (!SEG.empty())
     std::memcpy(p->image.data() + h.off_seg, SEG.data(), SEG.size() * sizeof(StreamSeg));
+  if (!TLEV.empty()) {
+    std::memcpy(p->image.data() + h.off_tlev, TLEV_OFF.data(), TLEV_OFF.size() * sizeof(int32_t));
+    std::memcpy(p->image.data() + align16(h.off_tlev + TLEV_OFF.size() * sizeof(int32_t)),
+                TLEV.data(), TLEV.size() * sizeof(uint2));
+  }
   p->n_vars = h.n_vars;
   p->n_t = h.n_t;
   p->n_rf = h.n_rf + 2 * h.n_rfp;
@@ -1116,6 +1179,8 @@ int validate_and_pack(const pccp_model_desc* d, Packed* p, int32_t bit0 = -1) {
   p->track_bytes = static_cast<uint32_t>(h.track_bytes);
   p->bit0 = h.bit0;
   p->n_slots = h.n_slots;
+  p->n_tlev = h.n_tlev;
+  p->tlev_bytes = static_cast<uint32_t>(h.core_bytes - h.off_tlev);
   return PCCP_OK;
 }
 
@@ -1250,6 +1315,7 @@ struct PropPlan {
   bool table_global;
   uint32_t copy_bytes;  // image prefix staged in shared memory (0: read in place)
   int stages;  // stream buffers per team (0: rows read in place)
+  uint32_t tlev_bytes;  // rows read in place: the temporal levels staged per CTA (0: none)
   int team, teams, grid, max_grid;
   size_t smem;
 };
@@ -1286,7 +1352,16 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   const int stages = global ? stream_stages_for(m->n_seg, cfg ? cfg->stream_table : 0, base,
                                                 per_team, teams, smem_max)
                             : 0;
-  const size_t smem = base + static_cast<size_t>(teams) * (per_team + stream_bytes(stages));
+  size_t smem = base + static_cast<size_t>(teams) * (per_team + stream_bytes(stages));
+  // rows read in place: the temporal rows' levels (a few KB) staged once per
+  // CTA when they fit, since their passes are chains of dependent loads
+  uint32_t tlev = 0;
+  if (global && stages == 0 && m->n_tlev > 0 &&
+      (levels_mask(cfg ? cfg->temporal_levels : 0, true) & 2) &&
+      smem + m->tlev_bytes <= static_cast<size_t>(smem_max)) {
+    tlev = m->tlev_bytes;
+    smem += tlev;
+  }
   const bool track = use_skip_stable(cfg ? cfg->skip_stable : 0, global);
   const auto kern =
       stages > 0 ? (track ? k_propagate<1024, 1, true, true, true>
@@ -1315,6 +1390,7 @@ int plan_propagate(const pccp_model* m, int32_t n_stores, const pccp_launch_conf
   p->table_global = global;
   p->copy_bytes = global ? 0u : img_smem;
   p->stages = stages;
+  p->tlev_bytes = tlev;
   p->team = team;
   p->teams = teams;
   p->max_grid = sms * per_sm;
@@ -1349,6 +1425,9 @@ int launch_propagate(const pccp_model* m, const PropPlan& plan, int32_t n_stores
   a.table_global = plan.table_global ? 1 : 0;
   a.stream_stages = plan.stages;
   a.reordered = m->reordered;
+  a.tlev_bytes = plan.tlev_bytes;
+  a.levels = levels_mask(cfg ? cfg->temporal_levels : 0, true);
+  a.off_tlev = m->core_bytes - m->tlev_bytes;
   const int grid = std::max(1, std::min((n_stores + plan.teams - 1) / plan.teams, plan.max_grid));
   plan.kern<<<grid, plan.team * plan.teams, plan.smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? PCCP_OK : PCCP_ERR_CUDA;
@@ -1536,6 +1615,7 @@ SolveArgs batch_args(const BatchPlan& p, const pccp_solve_opts* o, int32_t n) {
   a.mode = o->mode;
   a.strategy = o->strategy;
   a.obj_ub = o->obj_ub;
+  a.levels = levels_mask(o->temporal_levels, false);
   a.node_limit = o->node_limit;
   a.time_limit_ns = o->time_limit_ms > 0 ? o->time_limit_ms * 1000000ll : 0;
   a.max_image_bytes = 0;  // the streamed kernel reads every table from global memory
@@ -1671,6 +1751,8 @@ int pccp_model_create(const pccp_model_desc* desc_user, pccp_model** out) {
   m->image_bytes = static_cast<uint32_t>(p.image.size());
   m->core_bytes = p.core_bytes;
   m->track_bytes = p.track_bytes;
+  m->n_tlev = p.n_tlev;
+  m->tlev_bytes = p.tlev_bytes;
   m->bytes_per_sweep = p.bytes_per_sweep;
   m->n_seg = p.n_seg;
   m->reordered = 0;
@@ -1770,6 +1852,7 @@ int pccp_model_get_info(const pccp_model* m, pccp_model_info* info) {
   info->reordered = m->reordered;
   info->bool_vars = m->n_vars - m->bit0;
   info->store_bytes = 8 * m->n_slots;
+  info->temporal_levels = m->n_tlev;
   return PCCP_OK;
 }
 
@@ -2036,6 +2119,7 @@ int solve_parallel(const pccp_model* m, const pccp_solve_opts* o, pccp_result* r
     a.mode = o->mode;
     a.strategy = o->strategy;
     a.obj_ub = o->obj_ub;
+    a.levels = levels_mask(o->temporal_levels, false);
     a.track_words = track_words(m->n_vars, m->n_lin);
     a.table_global = global ? 1 : 0;
     a.stream_stages = stages;
@@ -2307,6 +2391,7 @@ void queue_opts_args(const pccp_solve_opts* o, QArgs* a) {
   a->mode = o->mode;
   a->strategy = o->strategy;
   a->obj_ub = o->obj_ub;
+  a->levels = levels_mask(o->temporal_levels, false);
   a->donate_nodes = o->donate_nodes < 0 ? -1 : (o->donate_nodes > 0 ? o->donate_nodes : 4);
   a->granularity = o->queue_granularity > 0 ? o->queue_granularity : 1;
   a->node_limit = o->node_limit;

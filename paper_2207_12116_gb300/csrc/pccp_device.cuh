@@ -38,7 +38,11 @@ struct TableHeader {
   // bit0 .. n_vars-1 (Booleans, when the model keeps them as bits) 32 to a
   // slot {lb bits, ub bits}; n_slots = bit0 + ceil((n_vars - bit0) / 32)
   int32_t bit0, n_slots;
-  int32_t pad2[2];
+  // temporal rows in topological levels (n_tlev > 0 when the rows x + d <= y
+  // form an acyclic graph over the variables): int32 level bounds
+  // [n_tlev + 1] at off_tlev, then (16-byte aligned) the rows grouped by the
+  // level of x, the length of the longest chain of rows ending at x
+  int32_t off_tlev, n_tlev;
 };
 static_assert(sizeof(TableHeader) == 128, "header must be 128 bytes");
 
@@ -94,7 +98,12 @@ struct Tab {
   const StreamSeg* seg;
   int n_seg;
   int bit0, n_slots;  // store layout (see TableHeader)
+  const int32_t* tlev_off;  // temporal rows in levels (see TableHeader); n_tlev 0: none
+  const uint2* tlev;
+  int n_tlev;
 };
+
+__host__ __device__ __forceinline__ int align16_dev(int x) { return (x + 15) & ~15; }
 
 __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
   const TableHeader* h = reinterpret_cast<const TableHeader*>(img);
@@ -125,7 +134,23 @@ __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
   tb.rfp = reinterpret_cast<const uint4*>(img + h->off_rfp);
   tb.bit0 = h->bit0;
   tb.n_slots = h->n_slots;
+  tb.n_tlev = h->n_tlev;
+  tb.tlev_off = reinterpret_cast<const int32_t*>(img + h->off_tlev);
+  tb.tlev = reinterpret_cast<const uint2*>(img + align16_dev(h->off_tlev + 4 * (h->n_tlev + 1)));
   return tb;
+}
+
+// The same with the temporal levels used only when `levels` is non-zero.
+__device__ __forceinline__ Tab make_tab(const uint8_t* img, int levels) {
+  Tab tb = make_tab(img);
+  if (!levels) tb.n_tlev = 0;
+  return tb;
+}
+
+// Point tb's temporal levels at a copy of their section (at p, 16-byte aligned).
+__device__ __forceinline__ void tab_levels_at(Tab& tb, const uint8_t* p) {
+  tb.tlev_off = reinterpret_cast<const int32_t*>(p);
+  tb.tlev = reinterpret_cast<const uint2*>(p + align16_dev(4 * (tb.n_tlev + 1)));
 }
 
 // ------------------------------------------------------------ PTX wrappers
@@ -161,6 +186,18 @@ __device__ __forceinline__ int atom_min_s32(int* p, int v) {
                : "r"(smem_u32(p)), "r"(v)
                : "memory");
   return old;
+}
+
+// The same joins without the old value (the caller knows from its snapshot
+// that the bound moves, unless another thread moved it further meanwhile).
+__device__ __forceinline__ void red_max_s32(int* p, int v) {
+  asm volatile("red.relaxed.cta.shared::cta.max.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v)
+               : "memory");
+}
+
+__device__ __forceinline__ void red_min_s32(int* p, int v) {
+  asm volatile("red.relaxed.cta.shared::cta.min.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v)
+               : "memory");
 }
 
 // Relaxed CTA-scope shared atomic OR / AND returning the old word (the joins
@@ -492,6 +529,91 @@ __device__ __forceinline__ void eval_temporal(const Sweep& w, uint2 row, Flags& 
   }
 }
 
+// The temporal rows level by level, by one warp (tb.n_tlev > 0): kUp, lower
+// bounds in increasing levels (lb y >= lb x + d); else upper bounds in
+// decreasing levels (ub x <= ub y - d).  A level's rows read only variables
+// that earlier levels of the pass have finished, so one pass carries a bound
+// along a whole chain of rows, where rows evaluated side by side move it one
+// row per sweep.  Only the order of evaluation changes: the fixed point is
+// the same (Sec. 3).  The next level's first row is loaded ahead.  A warp
+// runs it whole (the shuffles need every lane).
+template <bool kTrack, bool kUp>
+__device__ __forceinline__ void temporal_levels(const Sweep& w, const Team& tm, Flags& f) {
+  const Tab& tb = w.tb;
+  const int n = tb.n_tlev;
+  // level bounds: up to 31 levels held one per lane and read by shuffles
+  const bool in_regs = n < 32;
+  const int lane_off = in_regs && tm.lane <= n ? tb.tlev_off[tm.lane] : 0;
+  auto bound = [&](int l) {
+    return in_regs ? __shfl_sync(0xffffffffu, lane_off, l) : tb.tlev_off[l];
+  };
+  int L = kUp ? 0 : n - 1;
+  int lo = bound(L), hi = bound(L + 1);
+  uint2 row = lo + tm.lane < hi ? tb.tlev[lo + tm.lane] : make_uint2(0u, 0u);
+  for (int k = 0; k < n; ++k) {
+    const int Ln = kUp ? L + 1 : L - 1;
+    int nlo = 0, nhi = 0;
+    uint2 nrow = make_uint2(0u, 0u);
+    if (k + 1 < n) {
+      nlo = bound(Ln);
+      nhi = bound(Ln + 1);
+      if (nlo + tm.lane < nhi) nrow = tb.tlev[nlo + tm.lane];
+    }
+    for (int r = lo + tm.lane; r < hi; r += 32) {
+      if (r != lo + tm.lane) row = tb.tlev[r];
+      const int x = row.x & 0xffff, y = row.x >> 16, d = static_cast<int>(row.y);
+      const int2 X = ld_dom(w.st, x), Y = ld_dom(w.st, y);
+      // tells without a returned value, so the next level waits only for
+      // the loads; the change they report may also be another thread's
+      // (which moved the same bound in this sweep)
+      if (kUp) {
+        f.evals += 1;  // a row's two rules count as one evaluation
+        f.bytes += 20;
+        const int c = X.x + d;
+        if (c > Y.x) {
+          if (c > Y.y) {
+            f.fl = true;
+          } else {
+            red_max_s32(&w.st[y].x, c);
+            f.ch = true;
+            if (kTrack) mark_changed(w.tb, w.tk, w.cur, y);
+          }
+        }
+      } else {
+        const int c = Y.y - d;
+        if (c < X.y) {
+          if (c < X.x) {
+            f.fl = true;
+          } else {
+            red_min_s32(&w.st[x].y, c);
+            f.ch = true;
+            if (kTrack) mark_changed(w.tb, w.tk, w.cur, x);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    L = Ln;
+    lo = nlo;
+    hi = nhi;
+    row = nrow;
+  }
+}
+
+// Temporal rows of a sweep: in levels by the team's last two warps (one
+// warp for both passes in a one-warp team) when the table has levels, else
+// a thread per row.  Returns after this thread's share.
+template <bool kTrack>
+__device__ __forceinline__ void sweep_temporal(const Sweep& w, const Team& tm, Flags& f) {
+  const Tab& tb = w.tb;
+  if (tb.n_tlev > 0) {
+    if (tm.warp == tm.nwarps - 1) temporal_levels<kTrack, true>(w, tm, f);
+    if (tm.warp == (tm.nwarps > 1 ? tm.nwarps - 2 : 0)) temporal_levels<kTrack, false>(w, tm, f);
+  } else {
+    for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
+  }
+}
+
 // One reified row b <=> (A and B), A: x <= y, B: y <= x + d - 1, on a
 // snapshot X, Y, B: the four asks of [[phi <=> psi]] (Sec. 2) joined into the
 // candidate bounds (nlx .. nub start as the snapshot or earlier candidates).
@@ -785,8 +907,13 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
 template <bool kTrack, bool kQuiet, bool kBits>
 __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags& f) {
   const Tab& tb = w.tb;
+  // the warps that walk the temporal levels then take their share of the
+  // other rows too (leaving those to the other warps measured slower)
+  const bool lev = tb.n_tlev > 0;
+  const Team& dt = tm;
   if (kQuiet) {  // tables in global memory: linear, reified, temporal
-    for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) {
+    if (lev) sweep_temporal<kTrack>(w, tm, f);  // levels first
+    for (int r = dt.tid; r < tb.n_lin; r += dt.nthr) {
       if (skip_linear_short<kTrack>(w, r, f)) continue;
       const int4 h = tb.lin[r];
       eval_linear_thread_at<kTrack, kBits>(w, h, tb.terms + h.y, f);
@@ -810,21 +937,22 @@ __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags
         break;
       }
     }
-    for (int r = tm.tid; r < tb.n_rf; r += tm.nthr)
+    for (int r = dt.tid; r < tb.n_rf; r += dt.nthr)
       eval_reified<kTrack, kQuiet, kBits>(w, tb.rf[r], f);
-    for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
+    if (!lev) sweep_temporal<kTrack>(w, tm, f);
   } else {  // tables in shared memory: reified, temporal, linear
-    for (int r = tm.tid; r < tb.n_rfp; r += tm.nthr)
+    if (lev) sweep_temporal<kTrack>(w, tm, f);  // levels first
+    for (int r = dt.tid; r < tb.n_rfp; r += dt.nthr)
       eval_reified_pair<kTrack, kQuiet, kBits>(w, tb.rfp[r], f);
-    for (int r = tm.tid; r < tb.n_rf; r += tm.nthr)
+    for (int r = dt.tid; r < tb.n_rf; r += dt.nthr)
       eval_reified<kTrack, kQuiet, kBits>(w, tb.rf[r], f);
-    for (int r = tm.tid; r < tb.n_t; r += tm.nthr) eval_temporal<kTrack>(w, tb.t[r], f);
-    for (int r = tm.tid; r < tb.n_lin; r += tm.nthr) {
+    if (!lev) sweep_temporal<kTrack>(w, tm, f);
+    for (int r = dt.tid; r < tb.n_lin; r += dt.nthr) {
       if (skip_linear_short<kTrack>(w, r, f)) continue;
       const int4 h = tb.lin[r];
       eval_linear_thread_at<kTrack, kBits>(w, h, tb.terms + h.y, f);
     }
-    for (int r = tm.warp; r < tb.n_lin_long; r += tm.nwarps) {
+    for (int r = dt.warp; r < tb.n_lin_long; r += dt.nwarps) {
       if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
       const int4 h = tb.lin_long[r];
       eval_linear_warp_at<kTrack, kBits>(w, h, tb.terms_long + h.y, tm.lane, f);
