@@ -466,7 +466,22 @@ __global__ void __launch_bounds__(1024) k_solve_slots(SolveArgs a) {
       team_dfs<kTrackS, kLearned, false, false>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
                                                 a.witness + d.witness_off, out, X, nullptr);
     } else {
-      const Tab tb = make_tab(d.image, a.levels & 2);
+      Tab tb = make_tab(d.image, a.levels & 2);
+      // the temporal levels (a few KB walked as chains of dependent loads)
+      // into the slot after the store when they fit, else read in place
+      const uint32_t tl_off = static_cast<uint32_t>(__ldg(&hg->off_tlev));
+      const uint32_t tl = static_cast<uint32_t>(__ldg(&hg->core_bytes)) - tl_off;
+      if (tb.n_tlev > 0 && img_off + tl <= a.slot_bytes) {
+        if (!team_load_image(slot + img_off, d.image + tl_off, tl, mbar, parity, tm)) {
+          if (tm.tid == 0) {
+            out->status = PCCP_RES_LIMIT;
+            out->error = 3;
+          }
+          return;
+        }
+        parity ^= 1u;
+        tab_levels_at(tb, slot + img_off);
+      }
       const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
       team_dfs<kTrackG, kLearned, true, false>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
                                                a.witness + d.witness_off, out, X, nullptr);
@@ -1452,6 +1467,14 @@ uint32_t slot_need(const pccp_model* m, uint32_t off_store, bool track, bool sta
   return ((st_end + 127u) & ~127u) + (track ? m->track_bytes : m->core_bytes);
 }
 
+// Slot bytes of a model whose table is read in place, with its temporal
+// levels staged after the store when that fits in `room` (else without).
+uint32_t slot_need_global(const pccp_model* m, uint32_t off_store, uint32_t room) {
+  const uint32_t st_end = off_store + 8u * static_cast<uint32_t>(m->n_slots);
+  const uint32_t with = ((st_end + 127u) & ~127u) + m->tlev_bytes;
+  return m->n_tlev > 0 && with <= room ? with : st_end;
+}
+
 // Plans a batched search.  any_strategy: room for the learned strategy's
 // feature rows and an occupancy valid for every strategy's kernel (a batch
 // planned once for later searches).  Returns SMEM when some store does not
@@ -1547,7 +1570,8 @@ int plan_batch(const pccp_model* const* models, int32_t n, const pccp_solve_opts
   uint32_t want = 0;
   for (int32_t i = 0; i < n; ++i) {
     const uint32_t staged = slot_need(models[i], p->off_store, track_s, true);
-    const uint32_t need = staged <= room ? staged : slot_need(models[i], p->off_store, false, false);
+    const uint32_t need =
+        staged <= room ? staged : slot_need_global(models[i], p->off_store, room);
     want = std::max(want, need);
   }
   if (want > room) return PCCP_ERR_SMEM;  // a store alone does not fit
@@ -2301,13 +2325,20 @@ int plan_queue(const pccp_model* const* models, int32_t n, const pccp_solve_opts
   if (p->shared) {
     // one model: its table once per CTA, shared by the CTA's teams
     const pccp_model* m = models[0];
-    const uint32_t per = static_cast<uint32_t>(
+    uint32_t per = static_cast<uint32_t>(
         (p->off_store + 8ull * static_cast<uint32_t>(m->n_slots) + 127u) & ~127ull);
     const uint32_t img = track_s ? m->track_bytes : m->core_bytes;
     const uint32_t region = ((img + 127u) & ~127u) + 128u;
     p->table_global = m->bit0 < m->n_vars ||  // bit layouts are read in place
                       static_cast<size_t>(region) + per > static_cast<size_t>(smem_max);
     if (per > static_cast<uint32_t>(smem_max)) return PCCP_ERR_SMEM;
+    if (p->table_global) {  // room for the temporal levels after each team's store
+      const uint32_t with =
+          (slot_need_global(m, p->off_store, static_cast<uint32_t>(smem_max)) + 127u) & ~127u;
+      if (static_cast<size_t>(with) * std::max(1, static_cast<int>(o->teams_per_cta)) <=
+          static_cast<size_t>(smem_max))
+        per = with;
+    }
     p->shared_bytes = p->table_global ? 0u : img;
     p->shared_region = p->table_global ? 0u : region;
     int team = o->threads;
@@ -2340,7 +2371,7 @@ int plan_queue(const pccp_model* const* models, int32_t n, const pccp_solve_opts
     for (int32_t i = 0; i < n; ++i) {
       const uint32_t staged = slot_need(models[i], p->off_store, track_s, true);
       want = std::max(want, staged <= room ? staged
-                                           : slot_need(models[i], p->off_store, false, false));
+                                           : slot_need_global(models[i], p->off_store, room));
     }
     if (want > room) return PCCP_ERR_SMEM;
     p->shared_bytes = p->shared_region = 0;
