@@ -138,7 +138,7 @@ constexpr uint32_t kRightBit = 0x80000000u;
 // All control decisions are made by thread 0 and broadcast through shared
 // memory; every broadcast slot is written before a barrier and read after it,
 // and never rewritten before the next barrier that follows all its reads.
-template <bool kTrack, bool kLearned, bool kGlobal, bool kStream>
+template <bool kTrack, bool kLearned, bool kGlobal, bool kStream, int kBitSel = kBitsAny>
 __device__ __noinline__ void team_dfs(const Tab& tb, const int2* __restrict__ root, int2* st, const Team& tm,
                          SearchCtrl* sc, const Track& tk, int2* stack, const SolveArgs& a,
                          int max_iter, int32_t* witness, InstanceResult* out, uint32_t* X,
@@ -189,8 +189,8 @@ __device__ __noinline__ void team_dfs(const Tab& tb, const int2* __restrict__ ro
     if (sc->stop) break;
     int it = 0;
     const int fst =
-        team_fixpoint<kTrack, kGlobal, kStream>(tb, st, tm, &sc->fc, tk, !seeded, max_iter, it,
-                                                stream);
+        team_fixpoint<kTrack, kGlobal, kStream, kBitSel>(tb, st, tm, &sc->fc, tk, !seeded,
+                                                         max_iter, it, stream);
     if (tm.tid == 0) {
       ++S.nodes;
       S.iters += it;
@@ -483,8 +483,15 @@ __global__ void __launch_bounds__(1024) k_solve_slots(SolveArgs a) {
         tab_levels_at(tb, slot + img_off);
       }
       const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
-      team_dfs<kTrackG, kLearned, true, false>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
-                                               a.witness + d.witness_off, out, X, nullptr);
+      // one compilation each for models with and without Booleans as bits
+      if (tb.bit0 < tb.n_vars)
+        team_dfs<kTrackG, kLearned, true, false, kBitsYes>(tb, d.root, st, tm, sc, tk, stack, a,
+                                                           d.max_iter, a.witness + d.witness_off,
+                                                           out, X, nullptr);
+      else
+        team_dfs<kTrackG, kLearned, true, false, kBitsNo>(tb, d.root, st, tm, sc, tk, stack, a,
+                                                          d.max_iter, a.witness + d.witness_off,
+                                                          out, X, nullptr);
     }
   }
 }
