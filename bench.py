@@ -601,7 +601,8 @@ def run_gpu(args):
                        "the kernel over the CPU-GPU link)" if args.e2e_chunk < 0 else
                        "pccp_propagate_host (pinned host stores, copied in chunks of "
                        + (f"{args.e2e_chunk}" if args.e2e_chunk else "the library's size")
-                       + " overlapping the propagation)"),
+                       + " overlapping the propagation; the call's copies and launches "
+                         "captured in a CUDA graph on the first warm-up call and replayed)"),
                "timing": "host wall clock around each synchronous call"}
         if not args.no_probes:
             # the roof of this path: every store crosses the CPU-GPU link twice

@@ -225,9 +225,14 @@ int pccp_propagate_ex(const pccp_model* model, int32_t n_stores, int32_t* lb, in
  * in, propagate, copy out) through up to four device slots (page-locked
  * memory lets the copies overlap; pageable memory works but serialises
  * them); status and iterations, when mapped as above, are written by the
- * kernels where they lie instead of being copied.  Streams, events and
- * slots are created on the model's first such call, grown for larger chunks
- * and freed with the model; calls on one model are serialised (the host
+ * kernels where they lie instead of being copied.  When every array is
+ * page-locked, the call's copies and launches are captured once in a CUDA
+ * graph kept with the model and replayed, as one launch, by later calls
+ * with the same arrays, n_stores and chunk_stores (reuse the buffers to
+ * stay on that path; other arrays or sizes capture a new graph, which
+ * replaces the kept one).  Streams, events, slots and the graph are created
+ * on the model's first such call, grown for larger chunks and freed with
+ * the model; calls on one model are serialised (the host
  * thread waits for the one in progress).  Either way the transfers start
  * after the work already queued on `stream`, and later work on `stream`
  * follows them.  Synchronous: returns once every result is in host memory.

@@ -1607,7 +1607,10 @@ int plan_batch(const pccp_model* const* models, int32_t n, const pccp_solve_opts
     per_sm = std::min(per_sm, occ);
   }
   if (per_sm < 1) return PCCP_ERR_SMEM;
-  p->grid = std::max(1, std::min((n + teams - 1) / teams, sms * per_sm));
+  // one CTA per model up to the resident limit: models spread over the SMs
+  // before teams share one (a team's search is a chain of dependent nodes,
+  // so a model alone on an SM finishes first)
+  p->grid = std::max(1, std::min(static_cast<int>(n), sms * per_sm));
   if (o->blocks > 0) p->grid = std::min(p->grid, static_cast<int>(o->blocks));
   return PCCP_OK;
 }

@@ -123,6 +123,7 @@ def test_batch_shape_is_reported_and_bounded():
     models = [pccp.Model.from_rcpsp(config_instance("tiny8", s)) for s in range(5)]
     b = pccp.Batch(models, threads=64, teams_per_cta=6)
     threads, teams, ctas = b.shape
-    assert (threads, teams) == (64, 6) and ctas == 1  # 5 models fill one CTA's slots
+    # one CTA per model while SMs are free: models spread before teams share an SM
+    assert (threads, teams) == (64, 6) and ctas == 5
     with pytest.raises(pccp.PccpError):
         pccp.Batch(models, threads=128, teams_per_cta=16)

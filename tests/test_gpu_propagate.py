@@ -338,6 +338,48 @@ def test_host_default_chunking_large_batch():
     assert x + f == len(sample)
 
 
+def test_host_pipeline_graph_replays():
+    """With every array pinned, the chunked call is captured in a CUDA graph
+    on its first use and replayed by later calls on the same arrays: fresh
+    contents every call give the device entry point's results; other sizes,
+    chunkings and arrays capture anew, and going back recaptures; a pageable
+    status array takes the directly queued path on the same model."""
+    inst = config_instance("j30", 2)
+    m = pccp.Model.from_rcpsp(inst)
+    rows = pccp.rcpsp.build_rows(inst)
+    om = rcpsp_model(inst)
+    n = 1500
+    hlb = torch.empty((n, m.n_vars), dtype=torch.int32).pin_memory()
+    hub = torch.empty((n, m.n_vars), dtype=torch.int32).pin_memory()
+    st = torch.empty(n, dtype=torch.int32).pin_memory()
+    it = torch.empty(n, dtype=torch.int32).pin_memory()
+
+    def check(k, chunk, count, status=None):
+        nodes = draw_partial_assignments(inst.n, inst.horizon, count, seed=100 + k)
+        lb, ub = pccp.rcpsp.node_stores(rows, nodes)
+        plb, pub = hlb[:count], hub[:count]
+        plb.copy_(torch.from_numpy(lb))
+        pub.copy_(torch.from_numpy(ub))
+        s_ = st[:count] if status is None else status
+        pccp.propagate_host(m, plb, pub, s_, it[:count], chunk_stores=chunk)
+        dst, dlb, dub, _ = run(m, lb, ub)
+        fx = dst == 0
+        assert np.array_equal(s_.numpy(), dst), (k, chunk, count)
+        assert np.array_equal(plb.numpy()[fx], dlb[fx]) and np.array_equal(pub.numpy()[fx], dub[fx])
+        assert 0 < fx.sum() < count
+        x, f = compare_batch(om, lb, ub, s_.numpy(), plb.numpy(), pub.numpy(),
+                             rows=range(k, count, 97))
+        assert x + f == len(range(k, count, 97))
+
+    for k in range(3):
+        check(k, 0, n)
+    check(3, 400, n)
+    check(4, 0, 700)
+    check(5, 0, n)
+    check(6, 0, 300, status=torch.empty(300, dtype=torch.int32))
+    check(7, 0, n)
+
+
 def test_models_of_different_sizes_interleaved_and_threaded():
     """A small model planned between two calls on a larger one (same kernel,
     less shared memory) leaves the larger one launchable, in sequence and
