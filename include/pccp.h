@@ -221,7 +221,7 @@ int pccp_propagate_ex(const pccp_model* model, int32_t n_stores, int32_t* lb, in
  *                        allocation; the mapping is checked at both ends of
  *                        each array and INVALID returned if it is missing.
  * Chunked, while one chunk is propagated the next chunks are copied in and
- * the previous ones copied out, on three streams of the model's own (copy
+ * the previous ones copied out, on streams of the model's own (copy
  * in, propagate, copy out) through up to four device slots (page-locked
  * memory lets the copies overlap; pageable memory works but serialises
  * them); status and iterations, when mapped as above, are written by the
