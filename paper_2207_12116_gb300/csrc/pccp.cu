@@ -189,7 +189,7 @@ __device__ __noinline__ void team_dfs(const Tab& tb, const int2* __restrict__ ro
     if (sc->stop) break;
     int it = 0;
     const int fst =
-        team_fixpoint<kTrack, kGlobal, kStream, kBitSel>(tb, st, tm, &sc->fc, tk, !seeded,
+        team_fixpoint<kTrack, kGlobal, kStream, kBitSel, true>(tb, st, tm, &sc->fc, tk, !seeded,
                                                          max_iter, it, stream);
     if (tm.tid == 0) {
       ++S.nodes;
@@ -461,7 +461,8 @@ __global__ void __launch_bounds__(1024) k_solve_slots(SolveArgs a) {
         return;  // this team stops; its mbarrier phase may still be pending
       }
       parity ^= 1u;
-      const Tab tb = make_tab(img, a.levels & 1);
+      Tab tb = make_tab(img, a.levels & 1);
+      tb.lin_shift = lin_split_shift(tb, tm.nthr);
       const Track tk = make_track(track_base, tb.n_vars, tb.n_lin + tb.n_lin_long);
       team_dfs<kTrackS, kLearned, false, false>(tb, d.root, st, tm, sc, tk, stack, a, d.max_iter,
                                                 a.witness + d.witness_off, out, X, nullptr);

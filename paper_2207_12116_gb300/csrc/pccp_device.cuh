@@ -101,6 +101,9 @@ struct Tab {
   const int32_t* tlev_off;  // temporal rows in levels (see TableHeader); n_tlev 0: none
   const uint2* tlev;
   int n_tlev;
+  // short linear rows evaluated by groups of 2^lin_shift lanes (sweeps
+  // compiled with kSplit only; 0: a thread per row)
+  int lin_shift;
 };
 
 __host__ __device__ __forceinline__ int align16_dev(int x) { return (x + 15) & ~15; }
@@ -120,6 +123,7 @@ __device__ __forceinline__ Tab make_tab(const uint8_t* img) {
   tb.lin = reinterpret_cast<const int4*>(img + h->off_lin);
   tb.terms = reinterpret_cast<const uint32_t*>(img + h->off_terms);
   tb.n_lin_long = h->n_lin_long;
+  tb.lin_shift = 0;
   tb.lin_long = reinterpret_cast<const int4*>(img + h->off_lin_long);
   tb.terms_long = reinterpret_cast<const uint32_t*>(img + h->off_terms_long);
   tb.branch = reinterpret_cast<const int32_t*>(img + h->off_branch);
@@ -894,6 +898,81 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
   }
 }
 
+// Short row with header h evaluated by a group of G = 2^gs consecutive lanes
+// (lane j of the group takes terms j, j + G, ...): the sums of eval_linear_
+// thread_at reduced over the group by shuffles, then each lane tells its own
+// terms.  A row's chain of dependent loads shrinks G-fold, which pays where
+// one team's sweep waits on its longest row (a depth-first search alone on an
+// SM); every lane of a group computes the same S, so the tells are those of
+// the one-thread evaluation.  The group's terms share the row's bank of the
+// transposed tile (G-way bank conflicts on the term loads).
+template <bool kTrack>
+__device__ __forceinline__ void eval_linear_group_at(const Sweep& w, int4 h,
+                                                     const uint32_t* __restrict__ tp, int j,
+                                                     int gs, Flags& f) {
+  int2* st = w.st;
+  const int c = h.x, len = h.z, G = 1 << gs;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned gmask = ((1u << G) - 1u) << (lane & ~static_cast<unsigned>(G - 1));
+  if (j == 0) {
+    f.evals += 1;
+    f.bytes += 12 + 12 * len;
+  }
+  const bool pos = h.w & 1;
+  int S = 0, span = 0;
+#pragma unroll 4
+  for (int k = j; k < len; k += G) {
+    const uint32_t t = tp[32 * k];
+    const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
+    const int2 D = ld_var<false>(st, 0, v);
+    S += (pos || a > 0) ? a * D.x : a * D.y;
+    span = max(span, (pos || a > 0) ? a * (D.y - D.x) : a * (D.x - D.y));
+  }
+  for (int o = 1; o < G; o <<= 1) {
+    S += __shfl_xor_sync(gmask, S, o);
+    span = max(span, __shfl_xor_sync(gmask, span, o));
+  }
+  if (S > c) {
+    f.fl = true;
+    return;
+  }
+  if (S + span <= c) return;
+  if (h.w & 2) {  // 0/1 variables: as in eval_linear_thread_at
+    const int slack0 = c - S;
+    for (int k = j; k < len; k += G) {
+      const uint32_t t = tp[32 * k];
+      if ((static_cast<int>(t) >> 16) <= slack0) continue;
+      const int v = t & 0xffff;
+      const int2 D = ld_var<false>(st, 0, v);
+      if (D.x == 0 && D.y == 1) tell_ub_v<kTrack, false>(w, v, 0, D.x, D.y, f);
+    }
+    return;
+  }
+  for (int k = j; k < len; k += G) {
+    const uint32_t t = tp[32 * k];
+    const int v = t & 0xffff, a = static_cast<int>(t) >> 16;
+    const int2 D = ld_var<false>(st, 0, v);
+    const int mt = a > 0 ? a * D.x : a * D.y;
+    const int slack = c - (S - mt);
+    if (a > 0) {
+      if (a * D.y > slack) tell_ub<kTrack>(w, v, floor_div_pos(slack, a), D.x, D.y, f);
+    } else {
+      if (a * D.x > slack) tell_lb<kTrack>(w, v, -floor_div_pos(slack, -a), D.x, D.y, f);
+    }
+  }
+}
+
+// The lane-group shift for short linear rows of a team of nthr threads: the
+// largest G = 2^s <= 8 with G lanes for every row and at least 6 terms per
+// lane on the longest row (rows are stored longest first).
+__device__ __forceinline__ int lin_split_shift(const Tab& tb, int nthr) {
+  if (tb.n_lin <= 0) return 0;
+  const int len0 = tb.lin[0].z;
+  int s = 0;
+  while (s < 3 && (tb.n_lin << (s + 1)) <= nthr && (len0 >> (s + 1)) >= 6) ++s;
+  return s;
+}
+
 // One full evaluation of every row of the table (one iteration of the
 // eventless loop).  Rows of one kind run back to back so warps stay uniform:
 // a thread per reified, temporal and short linear row, a warp per long
@@ -904,7 +983,7 @@ __device__ __forceinline__ void eval_linear_thread_at(const Sweep& w, int4 h,
 // there (the second saves iterations on 120-task models, the first is
 // faster for the depth-first searches of 30-task models).  kBits: the model
 // keeps Booleans as bits (global tables only).
-template <bool kTrack, bool kQuiet, bool kBits>
+template <bool kTrack, bool kQuiet, bool kBits, bool kSplit = false>
 __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags& f) {
   const Tab& tb = w.tb;
   // the warps that walk the temporal levels then take their share of the
@@ -947,10 +1026,22 @@ __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags
     for (int r = dt.tid; r < tb.n_rf; r += dt.nthr)
       eval_reified<kTrack, kQuiet, kBits>(w, tb.rf[r], f);
     if (!lev) sweep_temporal<kTrack>(w, tm, f);
-    for (int r = dt.tid; r < tb.n_lin; r += dt.nthr) {
-      if (skip_linear_short<kTrack>(w, r, f)) continue;
-      const int4 h = tb.lin[r];
-      eval_linear_thread_at<kTrack, kBits>(w, h, tb.terms + h.y, f);
+    if (kSplit && !kBits && tb.lin_shift > 0) {
+      // groups of 2^gs consecutive lanes per row (u = tid + k nthr: a
+      // group's lanes share r, so they loop and skip together)
+      const int gs = tb.lin_shift;
+      for (int u = dt.tid; u < (tb.n_lin << gs); u += dt.nthr) {
+        const int r = u >> gs;
+        if (skip_linear_short<kTrack>(w, r, f)) continue;
+        const int4 h = tb.lin[r];
+        eval_linear_group_at<kTrack>(w, h, tb.terms + h.y, u & ((1 << gs) - 1), gs, f);
+      }
+    } else {
+      for (int r = dt.tid; r < tb.n_lin; r += dt.nthr) {
+        if (skip_linear_short<kTrack>(w, r, f)) continue;
+        const int4 h = tb.lin[r];
+        eval_linear_thread_at<kTrack, kBits>(w, h, tb.terms + h.y, f);
+      }
     }
     for (int r = dt.warp; r < tb.n_lin_long; r += dt.nwarps) {
       if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
@@ -1193,7 +1284,8 @@ __device__ __forceinline__ void count_sweeps(const Tab& tb, const Team& tm, FixC
 // kBitsNo / kBitsYes compile one sweep (models known to keep no Booleans as
 // bits / to keep some).
 constexpr int kBitsNo = 0, kBitsYes = 1, kBitsAny = 2;
-template <bool kTrack, bool kGlobal = false, bool kStream = false, int kBitSel = kBitsAny>
+template <bool kTrack, bool kGlobal = false, bool kStream = false, int kBitSel = kBitsAny,
+          bool kSplit = false>
 __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team& tm, FixCtrl* fc,
                                              const Track& tk, bool full, int max_iter,
                                              int& iters, Streamer* sm = nullptr) {
@@ -1223,7 +1315,7 @@ __device__ __forceinline__ int team_fixpoint(const Tab& tb, int2* st, const Team
     else if (kGlobal && kBitSel != kBitsNo && (kBitSel == kBitsYes || tb.bit0 < tb.n_vars))
       sweep_rows<kTrack, kGlobal, kGlobal>(w, tm, f);  // Booleans kept as bits
     else
-      sweep_rows<kTrack, kGlobal, false>(w, tm, f);
+      sweep_rows<kTrack, kGlobal, false, kSplit && !kGlobal>(w, tm, f);
     if (kTrack) {  // rows skipped vary: count what ran
       const int ev = __reduce_add_sync(0xffffffffu, f.evals);
       const int by = __reduce_add_sync(0xffffffffu, f.bytes);

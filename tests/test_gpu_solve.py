@@ -80,6 +80,36 @@ def test_generic_models_search():
         same(pccp.solve(m, mode=pccp.PCCP_COUNT_ALL), oracle.solve(om, mode=oracle.COUNT_ALL))
 
 
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+def test_lane_groups_for_linear_rows_are_exact(threads):
+    """In the depth-first searches over tables in shared memory, short linear
+    rows are summed by groups of 2, 4 or 8 lanes when the team has that many
+    lanes per row and the longest row at least 6 terms per lane (30-32-task
+    models: groups of 2 at 256 threads; 30-60-task models: 4 at 1024 threads;
+    generic models with a few rows of up to 64 terms: 8 at 1024 threads).
+    Node, failure and solution counts, optima and witnesses stay the
+    oracle's."""
+    insts = [config_instance("mixed30_60", s) for s in (0, 2, 3, 6, 14, 35)]
+    assert sorted({i.n for i in insts}) == [32, 47, 59, 60]
+    for strat, ostrat in ((pccp.PCCP_INPUT_ORDER, oracle.INPUT_ORDER),
+                          (pccp.PCCP_FIRST_FAIL, oracle.FIRST_FAIL)):
+        res = pccp.solve_batch([pccp.Model.from_rcpsp(i) for i in insts], node_limit=250,
+                               threads=threads, teams_per_cta=1, strategy=strat)
+        for inst, r in zip(insts, res):
+            same(r, oracle.solve(rcpsp_model(inst), node_limit=250, strategy=ostrat))
+    long_rows = 0
+    for seed in range(12):
+        gm = draw_generic_model(7700 + seed, n_int=8, n_bool=56, dom=10, n_temporal=6,
+                                n_linear=4, n_reified=10, max_len=64, coef=6)
+        lens = [sum(1 for a, _ in row[1] if a != 0) for row in gm.linear]
+        long_rows += max(lens) >= 48
+        m = pccp.Model.from_lists(gm.lb0, gm.ub0, gm.temporal, gm.linear, gm.reified,
+                                  gm.objective, gm.branch)
+        om = oracle_model_from_lists(gm)
+        same(pccp.solve(m, threads=threads, node_limit=300), oracle.solve(om, node_limit=300))
+    assert long_rows >= 4
+
+
 # ------------------------------------------- parallel search (EPS subproblems)
 
 from oracle import brute  # noqa: E402
