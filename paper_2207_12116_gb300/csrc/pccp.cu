@@ -1570,7 +1570,12 @@ int plan_batch(const pccp_model* const* models, int32_t n, const pccp_solve_opts
   if (team == 0 && o->props_per_thread > 0)
     team = std::min(1024 / teams, std::max(32, ((max_rows + o->props_per_thread - 1) /
                                                     o->props_per_thread + 31) & ~31));
-  if (team == 0) team = all_fit_one ? std::min(256, (1024 / teams) & ~31) : (1024 / teams) & ~31;
+  // default team: 256 threads when several share a CTA; a whole CTA when one
+  // team has it (its search is a chain of dependent sweeps, which the lane
+  // groups of the linear rows shorten with more lanes: 256 30-60-task models
+  // x 4,000 nodes in 353 ms at 1024 threads, 370 at 512, 401 at 256)
+  if (team == 0)
+    team = all_fit_one && teams > 1 ? std::min(256, (1024 / teams) & ~31) : (1024 / teams) & ~31;
   if (team < 32 || team * teams > 1024) return PCCP_ERR_INVALID;
   // slot size: what the largest model needs (staged when it fits), at most
   // an equal share of the CTA's shared memory

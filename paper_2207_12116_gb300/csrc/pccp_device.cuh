@@ -1019,6 +1019,49 @@ __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags
     for (int r = dt.tid; r < tb.n_rf; r += dt.nthr)
       eval_reified<kTrack, kQuiet, kBits>(w, tb.rf[r], f);
     if (!lev) sweep_temporal<kTrack>(w, tm, f);
+  } else if (kSplit && !kBits) {
+    // tables in shared memory, depth-first searches: the same order, with
+    // the table's fields read once into registers (the searches get the
+    // table by reference, and the loops' atomics through generic pointers
+    // would otherwise make every iteration reload them), and short linear
+    // rows by groups of 2^gs consecutive lanes (u = tid + k nthr: a group's
+    // lanes share r, so they loop and skip together)
+    const uint4* rfp = tb.rfp;
+    const uint2* rf = tb.rf;
+    const uint2* trow = tb.t;
+    const int4* lin = tb.lin;
+    const uint32_t* terms = tb.terms;
+    const int n_rfp = tb.n_rfp, n_rf = tb.n_rf, n_t = tb.n_t, n_lin = tb.n_lin;
+    const int n_lin_long = tb.n_lin_long, gs = tb.lin_shift;
+    if (lev) sweep_temporal<kTrack>(w, tm, f);  // levels first
+    for (int r = dt.tid; r < n_rfp; r += dt.nthr)
+      eval_reified_pair<kTrack, kQuiet, false>(w, rfp[r], f);
+    for (int r = dt.tid; r < n_rf; r += dt.nthr) eval_reified<kTrack, kQuiet, false>(w, rf[r], f);
+    if (!lev)
+      for (int r = dt.tid; r < n_t; r += dt.nthr) eval_temporal<kTrack>(w, trow[r], f);
+    if (gs > 0) {
+      for (int u = dt.tid; u < (n_lin << gs); u += dt.nthr) {
+        const int r = u >> gs;
+        if (skip_linear_short<kTrack>(w, r, f)) continue;
+        const int4 h = lin[r];
+        eval_linear_group_at<kTrack>(w, h, terms + h.y, u & ((1 << gs) - 1), gs, f);
+      }
+    } else {
+      for (int r = dt.tid; r < n_lin; r += dt.nthr) {
+        if (skip_linear_short<kTrack>(w, r, f)) continue;
+        const int4 h = lin[r];
+        eval_linear_thread_at<kTrack, false>(w, h, terms + h.y, f);
+      }
+    }
+    if (n_lin_long > 0) {
+      const int4* lin_long = tb.lin_long;
+      const uint32_t* terms_long = tb.terms_long;
+      for (int r = dt.warp; r < n_lin_long; r += dt.nwarps) {
+        if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
+        const int4 h = lin_long[r];
+        eval_linear_warp_at<kTrack, false>(w, h, terms_long + h.y, tm.lane, f);
+      }
+    }
   } else {  // tables in shared memory: reified, temporal, linear
     if (lev) sweep_temporal<kTrack>(w, tm, f);  // levels first
     for (int r = dt.tid; r < tb.n_rfp; r += dt.nthr)
@@ -1026,22 +1069,10 @@ __device__ __forceinline__ void sweep_rows(const Sweep& w, const Team& tm, Flags
     for (int r = dt.tid; r < tb.n_rf; r += dt.nthr)
       eval_reified<kTrack, kQuiet, kBits>(w, tb.rf[r], f);
     if (!lev) sweep_temporal<kTrack>(w, tm, f);
-    if (kSplit && !kBits && tb.lin_shift > 0) {
-      // groups of 2^gs consecutive lanes per row (u = tid + k nthr: a
-      // group's lanes share r, so they loop and skip together)
-      const int gs = tb.lin_shift;
-      for (int u = dt.tid; u < (tb.n_lin << gs); u += dt.nthr) {
-        const int r = u >> gs;
-        if (skip_linear_short<kTrack>(w, r, f)) continue;
-        const int4 h = tb.lin[r];
-        eval_linear_group_at<kTrack>(w, h, tb.terms + h.y, u & ((1 << gs) - 1), gs, f);
-      }
-    } else {
-      for (int r = dt.tid; r < tb.n_lin; r += dt.nthr) {
-        if (skip_linear_short<kTrack>(w, r, f)) continue;
-        const int4 h = tb.lin[r];
-        eval_linear_thread_at<kTrack, kBits>(w, h, tb.terms + h.y, f);
-      }
+    for (int r = dt.tid; r < tb.n_lin; r += dt.nthr) {
+      if (skip_linear_short<kTrack>(w, r, f)) continue;
+      const int4 h = tb.lin[r];
+      eval_linear_thread_at<kTrack, kBits>(w, h, tb.terms + h.y, f);
     }
     for (int r = dt.warp; r < tb.n_lin_long; r += dt.nwarps) {
       if (skip_linear_long<kTrack>(w, r, tm.lane, f)) continue;
