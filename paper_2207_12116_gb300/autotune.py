@@ -19,9 +19,9 @@ from . import Model, launch_config, propagate, solve, solve_batch, PccpError
 
 PROPAGATE_CANDIDATES = [(64, 4), (64, 8), (64, 15), (96, 5), (96, 10), (128, 2), (128, 4),
                         (128, 8), (160, 3), (192, 5), (256, 2), (256, 4), (512, 1)]
-SEARCH_THREADS = [64, 128, 256, 512]
+SEARCH_THREADS = [64, 128, 256, 512, 1024]
 # batched search: (teams per CTA, threads per team); 0 threads = rows-based
-SEARCH_SHAPES = [(1, 256), (1, 512), (2, 256), (2, 512), (3, 256), (4, 128), (4, 256),
+SEARCH_SHAPES = [(1, 256), (1, 512), (1, 1024), (2, 256), (2, 512), (3, 256), (4, 128), (4, 256),
                  (6, 128), (8, 128), (8, 64), (12, 64), (15, 64), (15, 32)]
 # parallel search of one model: (frontier subproblems per team, donation node budget)
 EPS_CANDIDATES = [(2, 0), (4, 0), (8, 0), (4, -1), (16, -1)]
