@@ -289,6 +289,7 @@ COMPLETE_FAMILY, COMPLETE_MODELS = "mixed6_10", 256
 COMPLETE_BATCH = True
 COMPLETE_SEQUENTIAL = True  # the one-team-per-model form too (about a minute)
 LEARNED_IN_BENCH = True     # train a policy (~20 s) and time the learned form
+SCALE_LEGS = True           # 60- and 120-task models, first-fail and learned (~30 s)
 
 
 def _graph_solve(pccp, batch, **kw):
@@ -392,6 +393,49 @@ def complete_batch_bench(pccp, policy=None, training=None):
     return out
 
 
+def scale_legs(pccp):
+    """Short forms of the 60-task learned-branching comparison and of the
+    120-task batch: a policy trained as in --learned (probe labels on 8- and
+    30-task nodes, 8 epochs); 64 seeded 60-task models (seeds 1000-1063),
+    5,000 nodes each, and 152 seeded 120-task models (seeds 2000-2151, tables
+    read from global memory), 1 s each; first-fail and learned, one launch
+    per strategy.  Per strategy: nodes/s, models with a schedule, their mean
+    best makespan; and model by model, whether the learned policy's best
+    makespan is lower, equal or higher.  No model of these sizes is proved
+    within such limits, so these are best-makespan-under-a-limit figures."""
+    pol, training = train_policy(argparse.Namespace(learned_epochs=8))
+    out = {}
+    for key, fam, seeds, limit, what in (
+            ("learned_60", "j60", range(1000, 1064), {"node_limit": 5000}, "5,000 nodes each"),
+            ("large_120", "j120", range(2000, 2152), {"time_limit_ms": 1000},
+             "1 s each, tables read from global memory")):
+        models = [pccp.Model.from_rcpsp(config_instance(fam, s)) for s in seeds]
+        leg = {"workload": f"{len(models)} seeded {fam[1:]}-task 4-resource models, one launch "
+                           f"per strategy, {what}"}
+        best = {}
+        for name, kw in (("first_fail", {"strategy": pccp.PCCP_FIRST_FAIL}),
+                         ("learned", {"strategy": pccp.PCCP_LEARNED, "policy": pol})):
+            res = pccp.solve_batch(models, **limit, **kw)
+            ms = res[0]["elapsed_ms"]
+            nodes = sum(r["nodes"] for r in res)
+            found = [r["objective"] for r in res if r["has_solution"]]
+            best[name] = [r["objective"] if r["has_solution"] else None for r in res]
+            leg[name] = {"kernel_ms": ms, "nodes": nodes, "nodes_per_s": nodes / (ms / 1000),
+                         "propagator_evals_per_s": sum(r["rows_evaluated"] for r in res)
+                         / (ms / 1000),
+                         "models_with_schedule": len(found),
+                         "mean_best_makespan": float(np.mean(found)) if found else None,
+                         "proven": sum(r["status"] != pccp.PCCP_RES_LIMIT for r in res)}
+        both = [(a, b) for a, b in zip(best["first_fail"], best["learned"])
+                if a is not None and b is not None]
+        leg["learned_better_equal_worse"] = [sum(b < a for a, b in both),
+                                             sum(b == a for a, b in both),
+                                             sum(b > a for a, b in both)]
+        leg["training"] = training
+        out[key] = leg
+    return out
+
+
 def search_bench(pccp, cpu=True):
     """Search throughput: (a) one persistent launch solving 256 seeded
     30-60-task models depth first, one team per model, each stopped after
@@ -419,6 +463,8 @@ def search_bench(pccp, cpu=True):
         if LEARNED_IN_BENCH:
             pol, training = train_policy_rollouts()
         out["batched_complete"] = complete_batch_bench(pccp, pol, training)
+    if SCALE_LEGS:
+        out.update(scale_legs(pccp))
     for key, fam, what in (("parallel", "j30", "30-task"), ("parallel_large", "j120", "120-task")):
         m = pccp.Model.from_rcpsp(config_instance(fam, 0))
         if EPS_NODE_LIMIT:
